@@ -1,0 +1,545 @@
+"""Pins of the FP64 oracle against facts other than itself.
+
+Each test checks the oracle against a closed form, an invariant, a textbook
+special case or brute force, chosen so that a plausible mistake (a dropped
+term, a wrong sign or index, a transposed operand, a different ordering of
+Algorithm 1) fails at least one of them.  CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2106_13281_gb300 import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def axis_angle(axis, ang):
+    axis = np.asarray(axis, dtype=np.float64) / np.linalg.norm(axis)
+    return np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+
+
+def single_body(mass=2.0, inertia=(0.3, 0.5, 0.7), g=(0, 0, 0), dt=0.05, substeps=10):
+    sb = S.SceneBuilder(dt=dt, substeps=substeps, gravity=g)
+    sb.body("b", mass, inertia, (0, 0, 0))
+    return sb.build()
+
+
+def state_of(desc, pos=None, quat=None, vel=None, ang=None, n=1):
+    B = len(desc["mass"])
+    st = np.zeros((n, B, 13))
+    st[:, :, 3] = 1.0
+    st[:, :, 0:3] = desc["rest_pos"]
+    st[:, :, 3:7] = desc["rest_rot"]
+    for k, v in ((0, pos), (3, quat), (7, vel), (10, ang)):
+        if v is not None:
+            st[:, 0, k:k + len(v)] = v
+    return st
+
+
+def rotmats(q):
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)
+    return R.reshape(q.shape[:-1] + (3, 3))
+
+
+def anchor_errors(desc, st):
+    R = rotmats(st[..., 3:7])
+    out = []
+    for j in range(len(desc["parent"])):
+        p, c = desc["parent"][j], desc["child"][j]
+        pp = st[..., p, :3] + np.einsum("...ij,j->...i", R[..., p, :, :], desc["parent_offset"][j])
+        pc = st[..., c, :3] + np.einsum("...ij,j->...i", R[..., c, :, :], desc["child_offset"][j])
+        out.append(np.linalg.norm(pp - pc, axis=-1))
+    return np.stack(out, -1)
+
+
+def no_contacts(desc):
+    d = dict(desc)
+    d["pair_a"] = np.zeros(0, dtype=np.int32)
+    d["pair_b"] = np.zeros(0, dtype=np.int32)
+    return d
+
+
+# ----------------------------------------------------------------- integrators
+def test_free_fall_closed_form():
+    """x_n = x0 + n h v0 + g h^2 n(n-1)/2 and v_n = v0 + n h g (Algorithm 1:
+    kinematic first, then the potential update)."""
+    g = (0.3, -0.2, -9.81)
+    d = single_body(g=g)
+    x0, v0 = np.array([0.1, -0.4, 2.0]), np.array([1.5, 0.25, 3.0])
+    st = state_of(d, pos=x0, vel=v0)
+    T = 7
+    out = orc.rollout(d, st, np.zeros((T, 1, 0)))
+    n, h = T * 10, 0.005
+    assert np.allclose(out[0, 0, 7:10], v0 + n * h * np.array(g), atol=1e-12, rtol=0)
+    assert np.allclose(out[0, 0, 0:3], x0 + n * h * v0 + np.array(g) * h * h * n * (n - 1) / 2, atol=1e-12, rtol=0)
+
+
+def test_free_spin_closed_form():
+    """Torque-free: w constant; q_n = Rot(w_hat, 2 n atan(h|w|/2)) q0 (world-frame update)."""
+    d = single_body(inertia=(0.2, 0.9, 1.7))
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=3) * 3.0
+    q0 = axis_angle(rng.normal(size=3), 1.1)
+    st = state_of(d, quat=q0, ang=w)
+    T = 5
+    out = orc.rollout(d, st, np.zeros((T, 1, 0)))
+    n, h = T * 10, 0.005
+    ang = 2 * n * math.atan(h * np.linalg.norm(w) / 2)
+    expect = qmul(axis_angle(w, ang), q0)
+    assert np.allclose(out[0, 0, 10:13], w, atol=1e-13)
+    assert np.allclose(out[0, 0, 3:7], expect, atol=1e-12)
+    assert abs(np.linalg.norm(out[0, 0, 3:7]) - 1) < 1e-13
+
+
+def hinge_system(gear=2.0, ca=0.5, I=0.8, lim=(-180, 180), kl=50.0, g=(0, 0, 0), dt=0.01, substeps=1, off=0.0,
+                 ka=40.0, c=5.0):
+    sb = S.SceneBuilder(dt=dt, substeps=substeps, gravity=g)
+    p = sb.body("P", 1.0, (1, 1, 1), (0, 0, 0), frozen_pos=(1, 1, 1), frozen_rot=(1, 1, 1))
+    cb = sb.body("C", 1.0, (I, I, I), (0, 0, -off))
+    j = sb.joint(p, cb, anchor=(0, 0, 0), axis=(1, 0, 0), ref=(0, 1, 0), stiffness=10000.0, spring_damping=c,
+                 angular_stiffness=ka, angular_damping=ca, limits=(lim,), limit_stiffness=kl)
+    sb.actuator(j, 0, gear)
+    return sb.build()
+
+
+def test_damped_hinge_closed_form():
+    """Frozen parent, child COM on the hinge axis at the anchor, no gravity,
+    constant torque: w_n = w_inf + (w0 - w_inf) rho^n with rho = 1 - h c_a/I,
+    w_inf = tau/c_a; angle_n = sum of 2 atan(h w_i / 2)."""
+    gear, ca, I, a = 2.0, 0.5, 0.8, 0.6
+    d = hinge_system(gear=gear, ca=ca, I=I)
+    st = orc.default_qp(d, 1)
+    w0 = 0.7
+    st[0, 1, 10:13] = [w0, 0, 0]
+    T = 400
+    out, tr = orc.rollout(d, st, np.full((T, 1, 1), a), traj=True)
+    h = 0.01
+    tau = gear * a
+    w_inf = tau / ca
+    rho = 1 - h * ca / I
+    n = np.arange(1, T + 1)
+    w_expect = w_inf + (w0 - w_inf) * rho ** n
+    assert np.allclose(tr[:, 0, 1, 10], w_expect, atol=1e-11, rtol=0)
+    w_prev = np.concatenate([[w0], w_expect[:-1]])
+    theta = np.cumsum(2 * np.arctan(h * w_prev / 2))
+    ang = np.array([orc.joint_angles(d, tr[t])[0, 0] for t in range(T)])
+    wrapped = np.angle(np.exp(1j * theta))
+    assert np.allclose(ang, wrapped, atol=1e-10)
+    # the anchors stay together and the hinge axes stay aligned
+    assert anchor_errors(d, tr).max() < 1e-12
+
+
+def test_hinge_limit_static_balance():
+    """Constant torque into the upper limit: at rest k_l (theta - hi) = tau."""
+    gear, kl = 10.0, 100.0
+    d = hinge_system(gear=gear, ca=1.0, I=1.0, lim=(-30, 30), kl=kl)
+    st = orc.default_qp(d, 1)
+    out = orc.rollout(d, st, np.full((4000, 1, 1), 1.0))
+    theta = orc.joint_angles(d, out)[0, 0]
+    assert abs(theta - (math.radians(30) + gear / kl)) < 1e-9
+    out2 = orc.rollout(d, st, np.full((4000, 1, 1), -1.0))
+    assert abs(orc.joint_angles(d, out2)[0, 0] - (math.radians(-30) - gear / kl)) < 1e-9
+
+
+def test_appendix_a_system_and_equilibrium():
+    """The App. A system matches the golden spec; hanging at rest its spring
+    stretches by m g / k (the steady state of the step)."""
+    gold = json.load(open(os.path.join(GOLDEN, "appendix_a.json")))
+    d = S.appendix_a()
+    assert d["substeps"] == gold["substeps"] and d["dt"] == gold["dt"]
+    assert np.allclose(d["gravity"], gold["gravity"])
+    for b, gb in enumerate(gold["bodies"]):
+        assert d["mass"][b] == gb["mass"] and np.allclose(d["inertia"][b], gb["inertia"])
+        assert list(d["frozen_pos"][b]) == gb["frozen_pos"] and list(d["frozen_rot"][b]) == gb["frozen_rot"]
+    assert d["stiffness"][0] == gold["joint"]["stiffness"]
+    assert np.allclose(d["child_offset"][0], gold["joint"]["child_offset"])
+    assert np.allclose([d["limit_lo"][0][0], d["limit_hi"][0][0]], gold["joint"]["angle_limit_deg"])
+    st = orc.default_qp(d, 1)
+    out = orc.rollout(d, st, np.zeros((3000, 1, 0)))
+    gap = anchor_errors(d, out)[0, 0]
+    assert abs(gap - 1.0 * 9.8 / 10000.0) < 1e-9
+    assert np.allclose(out[0, 0], st[0, 0])  # the frozen parent never moves
+
+
+def test_quaternion_norm_preserved():
+    d = S.quadruped()
+    rp, rr, ang = S.initial_conditions(d, 4, 0)
+    st = orc.default_qp(d, 4, rp, rr, ang)
+    a = S.actions(d, 4, 20, 0)
+    out = orc.rollout(d, st, a)
+    assert np.abs(np.linalg.norm(out[..., 3:7], axis=-1) - 1).max() < 1e-13
+
+
+# ----------------------------------------------------------------- contacts
+def sphere_scene(inertia=None, r=0.2, m=1.5, length=None, axis=(0, 0, 1), friction=1.0, baumgarte=0.1):
+    sb = S.SceneBuilder(dt=0.05, substeps=10, gravity=(0, 0, -9.81), baumgarte=baumgarte)
+    L = 2 * r if length is None else length
+    b = sb.capsule_body("s", m, r, L, (0, 0, 1.0), axis, friction=friction, inertia=inertia)
+    g = sb.plane(friction=1.0)
+    sb.pair(sb.collider_of(b), g)
+    return sb.build()
+
+
+def test_resting_sphere_height():
+    """Steady penetration d* = g h^2 / beta under Algorithm 1 (contacts see
+    the velocities before the potential update)."""
+    r, h, g, beta = 0.2, 0.005, 9.81, 0.1
+    d = sphere_scene(r=r)
+    st = state_of(d, pos=[0, 0, r])
+    out = orc.rollout(d, st, np.zeros((400, 1, 0)))
+    assert abs(out[0, 0, 2] - (r - g * h * h / beta)) < 1e-12
+    assert np.abs(out[0, 0, 7:13]).max() < 1e-12
+
+
+def test_resting_capsule_heights():
+    """Vertical capsule: one contact, same depth as the sphere.  Horizontal
+    capsule: two contacts averaged, d* = g h^2 / (alpha beta) with
+    alpha = (1/m) / (1/m + s^2 / I_t)."""
+    r, L, m, h, g, beta = 0.1, 0.6, 2.0, 0.005, 9.81, 0.1
+    s = L / 2 - r
+    I = S.capsule_inertia(m, r, L)
+    d = sphere_scene(r=r, length=L, m=m, inertia=I)
+    st = state_of(d, pos=[0, 0, s + r])
+    out = orc.rollout(d, st, np.zeros((400, 1, 0)))
+    assert abs(out[0, 0, 2] - (s + r - g * h * h / beta)) < 1e-12
+    dh = sphere_scene(r=r, length=L, m=m, inertia=I, axis=(1, 0, 0))
+    st = state_of(dh, pos=[0, 0, r])
+    out = orc.rollout(dh, st, np.zeros((400, 1, 0)))
+    alpha = (1 / m) / (1 / m + s * s / I[0])
+    assert abs(out[0, 0, 2] - (r - g * h * h / (alpha * beta))) < 1e-12
+
+
+def test_resting_box_height():
+    """Box on a plane: four corner contacts averaged, k_n = 1/m + hy^2/Ixx + hx^2/Iyy."""
+    m, half, h, g, beta = 0.5, np.array([0.05, 0.08, 0.03]), 0.005, 9.81, 0.1
+    sb = S.SceneBuilder(dt=0.05, substeps=10, gravity=(0, 0, -g))
+    I = S.box_inertia(m, half)
+    b = sb.body("box", m, I, (0, 0, 0))
+    bc = sb.collider(b, S.BOX, half=half)
+    sb.pair(bc, sb.plane())
+    d = sb.build()
+    st = state_of(d, pos=[0, 0, half[2]])
+    out = orc.rollout(d, st, np.zeros((400, 1, 0)))
+    kn = 1 / m + half[1] ** 2 / I[0] + half[0] ** 2 / I[1]
+    alpha = (1 / m) / kn
+    assert abs(out[0, 0, 2] - (half[2] - g * h * h / (alpha * beta))) < 1e-12
+
+
+def test_sliding_sphere_friction():
+    """Solid sphere (I = 2/5 m r^2) in converged contact given speed u0: while
+    sliding the speed drops by mu g h per substep; rolling sets in at 5/7 u0
+    (textbook), within O(h)."""
+    r, m, g, h, u0 = 0.2, 1.5, 9.81, 0.005, 2.0
+    I = 0.4 * m * r * r
+    d = sphere_scene(r=r, m=m, inertia=(I, I, I))
+    st = state_of(d, pos=[0, 0, r])
+    st = orc.rollout(d, st, np.zeros((100, 1, 0)))  # settle the contact
+    st[0, 0, 7:13] = [u0, 0, 0, 0, 0, 0]
+    d1 = dict(d, substeps=1, dt=h)
+    speeds = [u0]
+    cur = st
+    for _ in range(20):
+        cur = orc.rollout(d1, cur, np.zeros((1, 1, 0)))
+        speeds.append(cur[0, 0, 7])
+    dec = -np.diff(speeds[2:12])
+    assert np.allclose(dec, g * h, rtol=1e-6)
+    fin = orc.rollout(d, st, np.zeros((200, 1, 0)))
+    assert abs(fin[0, 0, 7] - 5.0 / 7.0 * u0) < 0.02 * u0
+    # rolling without slipping at the end: contact point velocity v - w_y r = 0
+    assert abs(fin[0, 0, 7] - fin[0, 0, 11] * r) < 1e-6
+
+
+def test_segment_closest_brute_force():
+    rng = np.random.default_rng(1)
+    cases = []
+    for _ in range(40):
+        cases.append(rng.normal(size=(4, 3)))
+    P = np.array([0.0, 0, 0])
+    cases.append(np.array([P, [1, 0, 0], [0, 0.5, 0], [1, 0.5, 0]]))      # parallel
+    cases.append(np.array([P, [1, 0, 0], [2, 0.5, 0], [3, 0.5, 0]]))      # collinear-ish, disjoint
+    cases.append(np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0.3], [0, 1, 0.3]]))  # crossing
+    cases.append(np.array([P, P, [0.3, 0.4, 0], [1, 2, 3]]))              # zero-length first
+    cases.append(np.array([[0.2, 0.1, 0], [1, 0, 1], [0.5, 0.5, 0.5], [0.5, 0.5, 0.5]]))  # zero-length second
+    grid = np.linspace(0, 1, 401)
+    for P1, Q1, P2, Q2 in cases:
+        s, t = orc.segment_closest(P1, Q1, P2, Q2)
+        assert -1e-15 <= s <= 1 + 1e-15 and -1e-15 <= t <= 1 + 1e-15
+        got = np.linalg.norm(P1 + s * (Q1 - P1) - P2 - t * (Q2 - P2))
+        A = P1[None, None, :] + grid[:, None, None] * (Q1 - P1)
+        Bp = P2[None, None, :] + grid[None, :, None] * (Q2 - P2)
+        dd = np.linalg.norm(A - Bp, axis=-1)
+        i, j = np.unravel_index(np.argmin(dd), dd.shape)
+        # local refinement of the sampled minimum
+        from scipy.optimize import minimize
+        f = lambda x: np.linalg.norm(P1 + np.clip(x[0], 0, 1) * (Q1 - P1) - P2 - np.clip(x[1], 0, 1) * (Q2 - P2))
+        best = min(dd[i, j], minimize(f, [grid[i], grid[j]], method="Nelder-Mead",
+                                      options=dict(xatol=1e-12, fatol=1e-14, maxiter=4000)).fun)
+        assert got <= best + 1e-9, (got, best)
+
+
+def test_capsule_box_brute_force():
+    rng = np.random.default_rng(2)
+    tgrid = np.linspace(0, 1, 20001)
+    n_hit = 0
+    for _ in range(60):
+        he = rng.uniform(0.05, 0.3, size=3)
+        c = rng.normal(size=3) * 0.2
+        q = axis_angle(rng.normal(size=3), rng.uniform(0, 3))
+        P = c + rng.normal(size=3) * 0.4
+        Q = c + rng.normal(size=3) * 0.4
+        r = rng.uniform(0.03, 0.2)
+        R = rotmats(q)
+        pts = P[None] + tgrid[:, None] * (Q - P)[None]
+        loc = (pts - c) @ R
+        res = loc - np.clip(loc, -he, he)
+        dist = np.linalg.norm(res, axis=1)
+        mind = dist.min()
+        out = orc.capsule_box(P, Q, r, c, q, he)
+        if mind > 1e-6:
+            if r - mind > 1e-6:
+                assert out is not None
+                depth, n, p = out
+                assert abs(depth - (r - mind)) < 1e-6
+                n_hit += 1
+            elif r - mind < -1e-6:
+                assert out is None
+    assert n_hit > 5
+
+
+def test_golden_section_parameter():
+    """The golden-section parameter minimises the convex segment-box distance."""
+    rng = np.random.default_rng(3)
+    tgrid = np.linspace(0, 1, 100001)
+    for _ in range(30):
+        he = rng.uniform(0.05, 0.3, size=3)
+        Pl = rng.normal(size=3) * 0.5
+        dl = rng.normal(size=3) * 0.5
+        t = orc.seg_box_param(Pl, dl, he)
+        f = lambda tt: np.sum((Pl + np.outer(tt, dl) - np.clip(Pl + np.outer(tt, dl), -he, he)) ** 2, axis=-1)
+        fg = f(tgrid)
+        if fg.min() < 1e-14:  # the segment enters the box: any point of the zero set
+            assert f(np.array([t]))[0] < 1e-12
+        else:  # strictly convex: within the final golden-section bracket of the minimiser
+            rho24 = (0.5 * (5 ** 0.5 - 1)) ** 24
+            assert abs(t - tgrid[np.argmin(fg)]) <= rho24 + 2e-5
+
+
+def test_box_plane_depth_is_lowest_corner():
+    sb = S.SceneBuilder()
+    half = np.array([0.1, 0.2, 0.05])
+    b = sb.body("box", 1.0, S.box_inertia(1.0, half), (0, 0, 0))
+    bc = sb.collider(b, S.BOX, half=half)
+    sb.pair(bc, sb.plane())
+    d = sb.build()
+    rng = np.random.default_rng(4)
+    signs = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    for _ in range(20):
+        q = axis_angle(rng.normal(size=3), rng.uniform(0, 3))
+        x = np.array([0.0, 0.0, rng.uniform(-0.1, 0.15)])
+        st = state_of(d, pos=x, quat=q)[0]
+        corners = x + (signs * half) @ rotmats(q).T
+        cts = orc.contacts(d, st)
+        below = corners[corners[:, 2] < 0]
+        assert len(cts) == len(below)
+        if len(below):
+            assert abs(max(c[2] for c in cts) + corners[:, 2].min()) < 1e-12
+
+
+# ----------------------------------------------------------------- invariants
+def test_linear_momentum_exact_without_gravity_and_contacts():
+    """Every joint and actuator term is equal and opposite: sum m v is constant
+    to roundoff with g = 0, no contacts, random actions and damping on."""
+    d = no_contacts(S.quadruped())
+    d["gravity"] = np.zeros(3)
+    rp, rr, ang = S.initial_conditions(d, 4, 5)
+    st = orc.default_qp(d, 4, rp, rr, ang)
+    st[:, :, 7:13] = np.random.default_rng(5).normal(size=st[:, :, 7:13].shape)
+    a = S.actions(d, 4, 40, 5)
+    _, m0 = orc.energy_momentum(d, st)
+    out = orc.rollout(d, st, a)
+    _, m1 = orc.energy_momentum(d, out)
+    scale = np.abs(m0[:, :3]).max() + 1
+    assert np.abs(m1[:, :3] - m0[:, :3]).max() < 1e-12 * scale * 1e3
+
+
+def test_angular_momentum_exact_isotropic_no_linear_damping():
+    """With isotropic inertia, no gravity, contacts or linear joint damping,
+    the step conserves angular momentum to roundoff: spring forces act along
+    the anchor separation and all torques come in equal and opposite pairs."""
+    d = no_contacts(S.quadruped())
+    d["gravity"] = np.zeros(3)
+    d["spring_damping"] = np.zeros_like(d["spring_damping"])
+    assert np.allclose(d["inertia"], 1.0)
+    rp, rr, ang = S.initial_conditions(d, 4, 6)
+    st = orc.default_qp(d, 4, rp, rr, ang)
+    st[:, :, 7:13] = np.random.default_rng(6).normal(size=st[:, :, 7:13].shape)
+    a = S.actions(d, 4, 40, 6)
+    _, m0 = orc.energy_momentum(d, st)
+    out = orc.rollout(d, st, a)
+    _, m1 = orc.energy_momentum(d, out)
+    assert np.abs(m1[:, 3:] - m0[:, 3:]).max() < 1e-9
+    # linear damping breaks it (the damper force is not along the separation)
+    d2 = dict(d, spring_damping=np.full_like(d["spring_damping"], 30.0))
+    _, m2 = orc.energy_momentum(d2, orc.rollout(d2, st, a))
+    assert np.abs(m2[:, 3:] - m0[:, 3:]).max() > 1e-6
+
+
+def astronaut(h_substeps, damping=False):
+    """The Sec. 6 conservation protocol: no damping, collisions or gravity."""
+    d = no_contacts(S.biped())
+    d["gravity"] = np.zeros(3)
+    if not damping:
+        d["spring_damping"] = np.zeros_like(d["spring_damping"])
+        d["angular_damping"] = np.zeros_like(d["angular_damping"])
+    d["substeps"] = h_substeps
+    return d
+
+
+def test_energy_drift_falls_with_step_size():
+    """Actuators off, random 1 m/s kicks, 1 s of simulation: the energy drift
+    shrinks as h shrinks (Sec. 6 energy protocol)."""
+    rng = np.random.default_rng(7)
+    drifts = []
+    for subs in (10, 20, 40):
+        d = astronaut(subs)
+        rp, rr, ang = S.initial_conditions(d, 8, 7, angle_sigma=0.05)
+        st = orc.default_qp(d, 8, rp, rr, ang)
+        kick = rng.normal(size=(8, st.shape[1], 3))
+        kick /= np.linalg.norm(kick, axis=-1, keepdims=True)
+        st[:, :, 7:10] = kick
+        rng = np.random.default_rng(7)
+        e0, _ = orc.energy_momentum(d, st)
+        out = orc.rollout(d, st, np.zeros((20, 8, len(d["gear"]))))
+        e1, _ = orc.energy_momentum(d, out)
+        drifts.append(np.mean(np.abs(e1 - e0) / e0))
+    assert drifts[0] < 0.1  # 7.6% at h = 5 ms, 2.5% at 2.5 ms, 1.5% at 1.25 ms
+    assert drifts[1] < drifts[0] and drifts[2] < drifts[1]
+
+
+def test_astronaut_momentum_protocol():
+    """Random ~0.5 N m actuation for 1 s with damping, collisions and gravity
+    off: linear momentum exact; angular momentum exact for these isotropic
+    bodies when the linear joint damper is off."""
+    d = astronaut(10)
+    d["gear"] = np.full_like(d["gear"], 0.5)
+    rp, rr, ang = S.initial_conditions(d, 8, 8)
+    st = orc.default_qp(d, 8, rp, rr, ang)
+    a = S.actions(d, 8, 20, 8)
+    _, m0 = orc.energy_momentum(d, st)
+    out = orc.rollout(d, st, a)
+    _, m1 = orc.energy_momentum(d, out)
+    assert np.abs(m1 - m0).max() < 1e-10
+
+
+# ----------------------------------------------------------------- default_qp / angles
+@pytest.mark.parametrize("name", ["quadruped", "biped", "pendulum", "arm_box", "appendix_a"])
+def test_default_qp_valid_configuration(name):
+    """default_qp places every joint's anchors together and reproduces the
+    requested joint angles (hinge angle and X-Y-Z Euler decomposition)."""
+    d = S.SCENES[name]()
+    rp, rr, ang = S.initial_conditions(d, 6, 9, height_jitter=0.05)
+    st = orc.default_qp(d, 6, rp, rr, ang)
+    if len(d["parent"]):
+        assert anchor_errors(d, st).max() < 1e-12
+        back = orc.joint_angles(d, st)
+        assert np.allclose(back, ang, atol=1e-12)
+    assert np.allclose(st[:, 0, 0:3], rp)
+    assert np.abs(np.linalg.norm(st[..., 3:7], axis=-1) - 1).max() < 1e-14
+
+
+def test_euler_round_trip_large_angles():
+    d = S.biped()
+    rng = np.random.default_rng(10)
+    D = S.n_dof(d)
+    ang = rng.uniform(-1.2, 1.2, size=(20, D))
+    st = orc.default_qp(d, 20, None, None, ang)
+    assert np.allclose(orc.joint_angles(d, st), ang, atol=1e-11)
+
+
+# ----------------------------------------------------------------- adjoint
+def small_quadruped_inputs(N=3, T=6, seed=11):
+    d = S.quadruped()
+    rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
+    st = orc.default_qp(d, N, rp, rr, ang)
+    st[:, 0, 2] -= 0.38  # start with feet near the ground so contacts occur
+    a = S.actions(d, N, T, seed).astype(np.float64)
+    return d, st, a
+
+
+def test_adjoint_dot_product():
+    """<u, J v> (forward-mode duals) equals <J^T u, v> (reverse-mode tape)."""
+    d, st, a = small_quadruped_inputs()
+    rng = np.random.default_rng(12)
+    u = rng.normal(size=st.shape)
+    v_s, v_a = rng.normal(size=st.shape), rng.normal(size=a.shape)
+    ds, _ = orc.jvp(d, st, a, v_s, v_a)
+    ga, gs = orc.vjp(d, st, a, u)
+    lhs = np.sum(u * ds)
+    rhs = np.sum(ga * v_a) + np.sum(gs * v_s)
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+    _, _, cc = orc.rollout(d, st, a, traj=True, contact_count=True)
+    assert cc.sum() > 0  # contacts took part
+
+
+def test_adjoint_vs_central_differences():
+    """FP64 central differences (h = 1e-6) of a scalar loss match the tape
+    gradient wherever the contact/limit active set is the same in both runs."""
+    d, st, a = small_quadruped_inputs(N=2, T=5)
+    rng = np.random.default_rng(13)
+    u = rng.normal(size=st.shape)
+    loss = lambda s, act: float(np.sum(u * orc.rollout(d, s, act)))
+    ga, gs = orc.vjp(d, st, a, u)
+    eps = 1e-6
+    checked = 0
+    for _ in range(30):
+        if rng.uniform() < 0.5:
+            idx = tuple(rng.integers(0, n) for n in a.shape)
+            ap, am = a.copy(), a.copy()
+            ap[idx] += eps
+            am[idx] -= eps
+            fd = (loss(st, ap) - loss(st, am)) / (2 * eps)
+            g = ga[idx]
+            c0 = orc.rollout(d, st, ap, contact_count=True)[1]
+            c1 = orc.rollout(d, st, am, contact_count=True)[1]
+        else:
+            n, b, k = rng.integers(0, st.shape[0]), rng.integers(0, st.shape[1]), rng.choice([0, 1, 2, 7, 8, 9, 10, 11, 12])
+            sp, sm = st.copy(), st.copy()
+            sp[n, b, k] += eps
+            sm[n, b, k] -= eps
+            fd = (loss(sp, a) - loss(sm, a)) / (2 * eps)
+            g = gs[n, b, k]
+            c0 = orc.rollout(d, sp, a, contact_count=True)[1]
+            c1 = orc.rollout(d, sm, a, contact_count=True)[1]
+        if not np.array_equal(c0, c1):
+            continue
+        assert abs(fd - g) <= 1e-4 * max(1.0, abs(g)), (fd, g)
+        checked += 1
+    assert checked >= 20
+
+
+def test_flop_counter_categories():
+    d = S.quadruped()
+    rp, rr, ang = S.initial_conditions(d, 2, 0)
+    st = orc.default_qp(d, 2, rp, rr, ang)
+    a = S.actions(d, 2, 3, 0)
+    counts, na = orc.flops(d, st, a)
+    for k in ("body", "joint", "actuator", "detect", "integrate"):
+        assert counts[k] > 0
+    # per-body work is per body and substep: 2 envs x 3 steps x 10 substeps x 9 bodies
+    assert counts["body"] % (2 * 3 * 10 * 9) == 0
