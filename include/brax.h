@@ -1,0 +1,206 @@
+/*
+ * brax.h - C ABI of the GB300 batched rigid-body step (Brax, arXiv 2106.13281).
+ *
+ * The library steps thousands of independent environments of one system (or a
+ * batch of systems) on one GPU and differentiates the rollout in reverse mode.
+ *
+ * State (the QP primitive of Sec. 3): per environment and body 13 floats,
+ *     pos[3], quat[4] (w, x, y, z; body-to-world), vel[3], angvel[3] (world),
+ * stored row-major as [n_envs, n_bodies, 13].  Actions are [T, n_envs,
+ * n_actuators] (one row per step, held over the step's substeps; Sec. 3:
+ * qp_{t+dt} = system.step(qp_t, actions)).  All floats are IEEE FP32.
+ *
+ * One step is `substeps` substeps of length dt/substeps (App. A).  One
+ * substep follows Algorithm 1 of Sec. 3: the kinematic integrator; joints,
+ * actuators and colliders evaluated on the same post-kinematic state; the
+ * potential integrator; the collision integrator.  Joints are springs
+ * (Sec. 7.1); contacts are velocity-level with Baumgarte stabilisation and
+ * every listed pair is tested every substep (Sec. 7.2).
+ *
+ * Conventions
+ *  - Every call returns a brax_status; the library never aborts or traps.
+ *  - Arrays passed to compute calls are device pointers unless stated,
+ *    contiguous, caller-owned; calls are asynchronous on `stream` (a
+ *    cudaStream_t passed as void*, NULL = the legacy default stream).
+ *  - Compute calls allocate nothing; scratch memory comes from the caller
+ *    (brax_workspace_size).  Device memory for a system's parameters and its
+ *    status word is allocated once by brax_system_create.
+ *  - Angles in the descriptor are degrees (App. A angle_limit); angles passed
+ *    to brax_default_qp are radians.
+ *  - Error messages: brax_last_error() (thread-local).
+ */
+#ifndef BRAX_GB300_H
+#define BRAX_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BRAX_DESC_VERSION 1
+
+/* Limits of one system (checked by brax_system_create). */
+#define BRAX_MAX_BODIES 32        /* one warp per body in a thread block */
+#define BRAX_MAX_POINTS 8         /* plane-contact points per body (box corners) */
+#define BRAX_MAX_CHILDREN 8       /* joints whose parent is one body */
+#define BRAX_MAX_PAIRS 128        /* body-body collider pairs per system */
+#define BRAX_MAX_BODY_PAIRS 24    /* body-body pairs touching one body */
+#define BRAX_MAX_PLANES 4
+
+typedef enum {
+  BRAX_OK = 0,
+  BRAX_ERR_INVALID_ARGUMENT = 1,   /* null pointer, size out of range, bad K or T */
+  BRAX_ERR_INVALID_DESCRIPTOR = 2, /* descriptor failed validation (message says why) */
+  BRAX_ERR_CUDA = 3,               /* a CUDA call failed (message has the CUDA error) */
+  BRAX_ERR_OUT_OF_MEMORY = 4,      /* allocation at create time failed */
+  BRAX_ERR_NONFINITE = 5,          /* a kernel saw a non-finite state (brax_sync_status) */
+  BRAX_ERR_TIMEOUT = 6,            /* reserved: a bounded device wait gave up */
+  BRAX_ERR_WORKSPACE = 7           /* workspace missing or smaller than brax_workspace_size */
+} brax_status;
+
+typedef enum { BRAX_PLANE = 0, BRAX_CAPSULE = 1, BRAX_BOX = 2 } brax_collider_type;
+
+/* Flat system specification (host memory, caller-owned, copied by
+ * brax_system_create).  The fields follow the system specification of
+ * Sec. 4.1 / App. A: bodies, joints, actuators, colliders and the collider
+ * pairs to test.  Counts: B bodies, J joints, A actuators, C colliders,
+ * P pairs. */
+typedef struct {
+  int32_t version; /* BRAX_DESC_VERSION */
+  int32_t n_bodies, n_joints, n_actuators, n_colliders, n_pairs;
+  int32_t substeps;             /* substeps per step (>= 1) */
+  float dt;                     /* step length (s) */
+  float gravity[3];
+  float baumgarte;              /* contact Baumgarte factor beta (Sec. 7.2) */
+  float contact_eps;            /* distance / speed below which a contact normal or
+                                   friction direction is undefined and skipped */
+  int32_t average_contacts;     /* 1: a body's contact update is the mean over its
+                                   active contacts; 0: the sum */
+  /* bodies [B] */
+  const float* mass;            /* [B] kg, > 0 */
+  const float* inertia;         /* [B][3] principal inertia in the body frame, > 0 */
+  const float* rest_pos;        /* [B][3] pose used by brax_default_qp for tree roots */
+  const float* rest_rot;        /* [B][4] */
+  const uint8_t* frozen_pos;    /* [B][3] 1 = world axis frozen (App. A "frozen") */
+  const uint8_t* frozen_rot;    /* [B][3] */
+  /* joints [J]: springs between a parent and a child body (Sec. 3, 7.1) */
+  const int32_t* parent;        /* [J] body index */
+  const int32_t* child;         /* [J] body index; a body is the child of at most one joint */
+  const int32_t* dof;           /* [J] 1 (hinge) or 3 */
+  const float* parent_offset;   /* [J][3] anchor in the parent frame */
+  const float* child_offset;    /* [J][3] anchor in the child frame */
+  const float* parent_frame;    /* [J][4] joint frame in the parent (x = hinge axis) */
+  const float* child_frame;     /* [J][4] joint frame in the child (equal to the
+                                   parent's at joint angle 0) */
+  const float* stiffness;       /* [J] anchor spring N/m */
+  const float* spring_damping;  /* [J] anchor damper N s/m */
+  const float* angular_stiffness; /* [J] hinge-axis alignment spring N m/rad */
+  const float* angular_damping; /* [J] N m s/rad (hinge: about the axis; 3-DOF: 3-D) */
+  const float* limit_lo;        /* [J][3] degrees */
+  const float* limit_hi;        /* [J][3] degrees */
+  const float* limit_stiffness; /* [J] N m/rad */
+  /* torque actuators [A] (Sec. 3: actions are torques) */
+  const int32_t* act_joint;     /* [A] joint index */
+  const int32_t* act_axis;      /* [A] 0..dof-1; at most one actuator per (joint, axis) */
+  const float* gear;            /* [A] torque = gear * clamp(action, -1, 1) */
+  /* colliders [C] */
+  const int32_t* col_body;      /* [C] body index; -1 = static world (planes only) */
+  const int32_t* col_type;      /* [C] brax_collider_type */
+  const float* col_pos;         /* [C][3] in the body frame (plane: a point) */
+  const float* col_rot;         /* [C][4] in the body frame (plane: z = normal; capsule: z = axis) */
+  const float* radius;          /* [C] capsule radius */
+  const float* length;          /* [C] capsule length, tip to tip */
+  const float* half_extents;    /* [C][3] box half extents */
+  const float* friction;        /* [C] pair friction = product */
+  const float* elasticity;      /* [C] pair elasticity = product */
+  /* pairs [P] tested every substep (Sec. 7.2): capsule-plane, box-plane,
+   * capsule-capsule, capsule-box (either order) */
+  const int32_t* pair_a;        /* [P] collider index */
+  const int32_t* pair_b;        /* [P] collider index */
+} brax_desc;
+
+typedef struct brax_system brax_system;
+typedef struct brax_batch brax_batch;
+
+/* Validate a descriptor (Sec. 4.1 system specification) and upload its
+ * parameters to the current CUDA device.  On success *out owns device
+ * memory until brax_system_destroy.  Errors: INVALID_ARGUMENT (null),
+ * INVALID_DESCRIPTOR (with a message naming the field), CUDA, OUT_OF_MEMORY. */
+int brax_system_create(const brax_desc* desc, brax_system** out);
+void brax_system_destroy(brax_system* sys);
+
+/* Sizes of a system: bodies, actuators, total joint DOF. Any out pointer may be NULL. */
+int brax_system_info(const brax_system* sys, int32_t* n_bodies, int32_t* n_actuators, int32_t* n_dof);
+
+/* default_qp (Sec. 4.1): place every body of each environment in a valid
+ * joint configuration.  Roots keep their rest pose; body 0 takes root_pos
+ * [N,3] and root_rot [N,4] when given; joint angles [N, n_dof] (radians,
+ * joint order, axes 0..dof-1) default to 0.  Velocities are zero.
+ * Output state_out [N, B, 13].  Device pointers; any input may be NULL. */
+int brax_default_qp(const brax_system* sys, int64_t n_envs, const float* root_pos, const float* root_rot,
+                    const float* joint_angles, float* state_out, void* stream);
+
+/* One step (Sec. 3): state_out = step(state_in, actions).  state [N,B,13],
+ * actions [N,A].  state_out may alias state_in. */
+int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, const float* actions, float* state_out,
+              void* stream);
+
+/* T steps in one persistent launch: the state stays on chip for the whole
+ * rollout; only actions stream in.  Outputs (device, NULL to skip):
+ *   state_T       [N,B,13] state after T steps (required);
+ *   checkpoints   [ceil(T/K), N, B, 13]: the state at steps 0, K, 2K, ... (the
+ *                 input of brax_rollout_backward; K >= 1);
+ *   torso_traj    [T, N, 3]: body 0's position after every step;
+ *   contact_count [N] int32: active contacts summed over all substeps. */
+int brax_rollout(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                 const float* actions, float* state_T, float* checkpoints, float* torso_traj,
+                 int32_t* contact_count, void* stream);
+
+/* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K). */
+int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, size_t* bytes);
+
+/* Reverse-mode gradient of a rollout (the differentiable step, Sec. 1 and
+ * Sec. 5 APG).  Inputs: state0, actions and the checkpoints written by
+ * brax_rollout with the same K; cotangents g_state_T [N,B,13] (required)
+ * and g_torso_traj [T,N,3] (NULL = zero).  Outputs g_actions [T,N,A] and
+ * g_state0 [N,B,13] (either may be NULL).  The forward is recomputed from
+ * each checkpoint segment on chip.  workspace: device scratch of at least
+ * brax_workspace_size bytes, 256-byte aligned. */
+int brax_rollout_backward(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                          const float* actions, const float* checkpoints, const float* g_state_T,
+                          const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Heterogeneous batch (systems of different sizes in one launch).  Arrays
+ * of a batch are the concatenation over systems i of the per-system arrays
+ * (state blocks [N_i, B_i, 13], action blocks [T, N_i, A_i], torso blocks
+ * [T, N_i, 3], checkpoint blocks [ceil(T/K), N_i, B_i, 13]).  The systems
+ * must outlive the batch. */
+int brax_batch_create(const brax_system* const* systems, const int64_t* n_envs, int32_t n_systems,
+                      brax_batch** out);
+void brax_batch_destroy(brax_batch* batch);
+/* Element offsets of system i's blocks in the concatenated arrays. */
+int brax_batch_offsets(const brax_batch* batch, int32_t T, int32_t K, int32_t i, int64_t* state_off,
+                       int64_t* action_off, int64_t* torso_off, int64_t* ckpt_off);
+int brax_batch_rollout(const brax_batch* batch, int32_t T, int32_t K, const float* state0, const float* actions,
+                       float* state_T, float* checkpoints, float* torso_traj, void* stream);
+int brax_batch_workspace_size(const brax_batch* batch, int32_t T, int32_t K, size_t* bytes);
+int brax_batch_rollout_backward(const brax_batch* batch, int32_t T, int32_t K, const float* state0,
+                                const float* actions, const float* checkpoints, const float* g_state_T,
+                                const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Synchronise `stream`, then read and clear the system's device status word:
+ * BRAX_OK, or BRAX_ERR_NONFINITE if any kernel since the last call produced
+ * a non-finite state.  Also reports a pending CUDA error as BRAX_ERR_CUDA. */
+int brax_sync_status(const brax_system* sys, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* brax_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRAX_GB300_H */

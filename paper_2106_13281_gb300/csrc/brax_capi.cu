@@ -1,0 +1,644 @@
+// C ABI of the batched step: descriptor validation, the device parameter
+// blob, launch configuration, status words.  Declarations and contracts are
+// in include/brax.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/brax.h"
+#include "brax_kernels.h"
+#include "brax_params.h"
+
+using namespace brax;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(BRAX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ host quaternion helpers (double)
+void dq_normalize(double* q) {
+  double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+void dq_rotate(const double* q, const double* v, double* o) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                    {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                    {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+  for (int i = 0; i < 3; ++i) o[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
+}
+void dq_matrix(const double* q, double R[3][3]) {
+  double e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, c[3];
+  for (int j = 0; j < 3; ++j) {
+    dq_rotate(q, e[j], c);
+    for (int i = 0; i < 3; ++i) R[i][j] = c[i];
+  }
+}
+bool finite_all(const float* p, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+struct Rejected {
+  std::string msg;
+};
+#define REQUIRE(cond, msg)                  \
+  do {                                      \
+    if (!(cond)) throw Rejected{std::string(msg)}; \
+  } while (0)
+
+// Validate a descriptor and flatten it into the parameter blob.
+std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int* P_out) {
+  REQUIRE(d.version == BRAX_DESC_VERSION, "version: expected BRAX_DESC_VERSION");
+  const int B = d.n_bodies, J = d.n_joints, A = d.n_actuators, C = d.n_colliders, P = d.n_pairs;
+  REQUIRE(B >= 1 && B <= BRAX_MAX_BODIES, "n_bodies: must be in [1, BRAX_MAX_BODIES]");
+  REQUIRE(J >= 0 && J < B, "n_joints: must be in [0, n_bodies - 1]");
+  REQUIRE(A >= 0 && C >= 0 && P >= 0, "counts must be non-negative");
+  REQUIRE(d.substeps >= 1 && d.substeps <= 1000, "substeps: must be in [1, 1000]");
+  REQUIRE(std::isfinite(d.dt) && d.dt > 0.f, "dt: must be positive and finite");
+  REQUIRE(finite_all(d.gravity, 3), "gravity: must be finite");
+  REQUIRE(std::isfinite(d.baumgarte) && d.baumgarte >= 0.f, "baumgarte: must be finite and >= 0");
+  REQUIRE(std::isfinite(d.contact_eps) && d.contact_eps > 0.f, "contact_eps: must be positive");
+  REQUIRE(d.mass && d.inertia && d.rest_pos && d.rest_rot && d.frozen_pos && d.frozen_rot, "body arrays: null");
+  if (J > 0)
+    REQUIRE(d.parent && d.child && d.dof && d.parent_offset && d.child_offset && d.parent_frame && d.child_frame &&
+                d.stiffness && d.spring_damping && d.angular_stiffness && d.angular_damping && d.limit_lo &&
+                d.limit_hi && d.limit_stiffness,
+            "joint arrays: null");
+  if (A > 0) REQUIRE(d.act_joint && d.act_axis && d.gear, "actuator arrays: null");
+  if (C > 0)
+    REQUIRE(d.col_body && d.col_type && d.col_pos && d.col_rot && d.radius && d.length && d.half_extents &&
+                d.friction && d.elasticity,
+            "collider arrays: null");
+  if (P > 0) REQUIRE(d.pair_a && d.pair_b, "pair arrays: null");
+  for (int b = 0; b < B; ++b) {
+    REQUIRE(std::isfinite(d.mass[b]) && d.mass[b] > 0.f, "mass: must be positive and finite");
+    for (int i = 0; i < 3; ++i) REQUIRE(std::isfinite(d.inertia[3 * b + i]) && d.inertia[3 * b + i] > 0.f,
+                                        "inertia: must be positive and finite");
+  }
+  REQUIRE(finite_all(d.rest_pos, 3 * B) && finite_all(d.rest_rot, 4 * B), "rest pose: must be finite");
+
+  const int Pb_max = BRAX_MAX_PAIRS;
+  std::vector<SysP> sysv(1);
+  SysP& S = sysv[0];
+  std::memset(&S, 0, sizeof(S));
+  std::vector<BodyP> bodies(B);
+  std::memset(bodies.data(), 0, sizeof(BodyP) * B);
+  for (int b = 0; b < B; ++b) {
+    BodyP& bp = bodies[b];
+    bp.inv_mass = (float)(1.0 / d.mass[b]);
+    uint32_t fl = 0;
+    for (int i = 0; i < 3; ++i) {
+      bp.inv_I[i] = (float)(1.0 / d.inertia[3 * b + i]);
+      if (d.frozen_pos[3 * b + i]) fl |= kFrozenPos0 << i;
+      if (d.frozen_rot[3 * b + i]) fl |= kFrozenRot0 << i;
+    }
+    if (fl) fl |= kAnyFrozen;
+    bp.flags = fl;
+    bp.parent = -1;
+    bp.joint = -1;
+    bp.dof = 0;
+    for (int i = 0; i < 3; ++i) {
+      bp.act[i] = -1;
+      bp.rest_pos[i] = d.rest_pos[3 * b + i];
+    }
+    double rq[4] = {d.rest_rot[4 * b], d.rest_rot[4 * b + 1], d.rest_rot[4 * b + 2], d.rest_rot[4 * b + 3]};
+    REQUIRE(rq[0] * rq[0] + rq[1] * rq[1] + rq[2] * rq[2] + rq[3] * rq[3] > 1e-12, "rest_rot: zero quaternion");
+    dq_normalize(rq);
+    for (int i = 0; i < 4; ++i) bp.rest_rot[i] = (float)rq[i];
+  }
+  // joints
+  const double deg = 3.14159265358979323846 / 180.0;
+  int D = 0;
+  for (int j = 0; j < J; ++j) {
+    const int p = d.parent[j], c = d.child[j];
+    REQUIRE(p >= 0 && p < B && c >= 0 && c < B && p != c, "joint parent/child: out of range or equal");
+    REQUIRE(d.dof[j] == 1 || d.dof[j] == 3, "dof: must be 1 or 3");
+    BodyP& bc = bodies[c];
+    REQUIRE(bc.joint < 0, "child: a body may be the child of only one joint");
+    REQUIRE(bodies[p].n_children < BRAX_MAX_CHILDREN, "parent: more than BRAX_MAX_CHILDREN children");
+    bodies[p].children[bodies[p].n_children++] = c;
+    bodies[p].flags |= kPublish;
+    bc.joint = j;
+    bc.parent = p;
+    bc.dof = d.dof[j];
+    bc.flags |= kHasParent;
+    bc.dof_offset = D;
+    D += d.dof[j];
+    REQUIRE(finite_all(d.parent_offset + 3 * j, 3) && finite_all(d.child_offset + 3 * j, 3), "offsets: not finite");
+    for (int i = 0; i < 3; ++i) {
+      bc.off_p[i] = d.parent_offset[3 * j + i];
+      bc.off_c[i] = d.child_offset[3 * j + i];
+    }
+    double fp[4], fc[4];
+    for (int i = 0; i < 4; ++i) {
+      fp[i] = d.parent_frame[4 * j + i];
+      fc[i] = d.child_frame[4 * j + i];
+    }
+    REQUIRE(fp[0] * fp[0] + fp[1] * fp[1] + fp[2] * fp[2] + fp[3] * fp[3] > 1e-12 &&
+                fc[0] * fc[0] + fc[1] * fc[1] + fc[2] * fc[2] + fc[3] * fc[3] > 1e-12,
+            "joint frames: zero quaternion");
+    dq_normalize(fp);
+    dq_normalize(fc);
+    const double e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int a = 0; a < 3; ++a) {
+      double o[3];
+      dq_rotate(fp, e[a], o);
+      for (int i = 0; i < 3; ++i) bc.ap[3 * a + i] = (float)o[i];
+      dq_rotate(fc, e[a], o);
+      for (int i = 0; i < 3; ++i) bc.ac[3 * a + i] = (float)o[i];
+    }
+    for (int i = 0; i < 4; ++i) {
+      bc.frame_p[i] = (float)fp[i];
+      bc.frame_c[i] = (float)fc[i];
+    }
+    const float kk[5] = {d.stiffness[j], d.spring_damping[j], d.angular_stiffness[j], d.angular_damping[j],
+                         d.limit_stiffness[j]};
+    for (float v : kk) REQUIRE(std::isfinite(v) && v >= 0.f, "joint constants: must be finite and >= 0");
+    bc.k = kk[0];
+    bc.c = kk[1];
+    bc.ka = kk[2];
+    bc.ca = kk[3];
+    bc.kl = kk[4];
+    for (int a = 0; a < 3; ++a) {
+      REQUIRE(std::isfinite(d.limit_lo[3 * j + a]) && std::isfinite(d.limit_hi[3 * j + a]), "limits: not finite");
+      bc.lo[a] = (float)(d.limit_lo[3 * j + a] * deg);
+      bc.hi[a] = (float)(d.limit_hi[3 * j + a] * deg);
+    }
+  }
+  // topological order of joints (children of placed bodies)
+  {
+    std::vector<int> placed(B, 0);
+    for (int b = 0; b < B; ++b) placed[b] = bodies[b].joint < 0;
+    int n = 0;
+    for (int pass = 0; pass <= J && n < J; ++pass)
+      for (int b = 0; b < B; ++b)
+        if (!placed[b] && bodies[b].joint >= 0 && placed[bodies[b].parent]) {
+          S.joint_order[n++] = b;
+          placed[b] = 1;
+        }
+    REQUIRE(n == J, "joints: the joint graph has a cycle");
+    S.n_order = n;
+  }
+  // actuators
+  for (int k = 0; k < A; ++k) {
+    const int j = d.act_joint[k];
+    REQUIRE(j >= 0 && j < J, "act_joint: out of range");
+    const int c = d.child[j];
+    const int ax = d.act_axis[k];
+    REQUIRE(ax >= 0 && ax < d.dof[j], "act_axis: out of range for the joint's dof");
+    REQUIRE(bodies[c].act[ax] < 0, "actuators: at most one actuator per (joint, axis)");
+    REQUIRE(std::isfinite(d.gear[k]), "gear: not finite");
+    bodies[c].act[ax] = k;
+    bodies[c].gear[ax] = d.gear[k];
+  }
+  // colliders, planes
+  std::vector<int> plane_slot(C, -1);
+  std::vector<PlaneP> planes;
+  for (int c = 0; c < C; ++c) {
+    const int t = d.col_type[c];
+    REQUIRE(t == BRAX_PLANE || t == BRAX_CAPSULE || t == BRAX_BOX, "col_type: unknown");
+    REQUIRE(finite_all(d.col_pos + 3 * c, 3) && finite_all(d.col_rot + 4 * c, 4), "collider pose: not finite");
+    if (t == BRAX_PLANE) {
+      REQUIRE(d.col_body[c] == -1, "planes must be static (col_body -1)");
+      REQUIRE((int)planes.size() < BRAX_MAX_PLANES, "more than BRAX_MAX_PLANES planes");
+      double q[4] = {d.col_rot[4 * c], d.col_rot[4 * c + 1], d.col_rot[4 * c + 2], d.col_rot[4 * c + 3]};
+      dq_normalize(q);
+      const double ez[3] = {0, 0, 1};
+      double n[3];
+      dq_rotate(q, ez, n);
+      PlaneP pl;
+      for (int i = 0; i < 3; ++i) {
+        pl.p0[i] = d.col_pos[3 * c + i];
+        pl.n[i] = (float)n[i];
+      }
+      plane_slot[c] = (int)planes.size();
+      planes.push_back(pl);
+    } else {
+      REQUIRE(d.col_body[c] >= 0 && d.col_body[c] < B, "col_body: capsules and boxes need a body");
+      if (t == BRAX_CAPSULE)
+        REQUIRE(d.radius[c] > 0.f && d.length[c] >= 0.f && std::isfinite(d.radius[c]) && std::isfinite(d.length[c]),
+                "capsule: radius > 0, length >= 0");
+      else
+        for (int i = 0; i < 3; ++i) REQUIRE(d.half_extents[3 * c + i] > 0.f, "box: half extents must be > 0");
+    }
+    REQUIRE(std::isfinite(d.friction[c]) && d.friction[c] >= 0.f, "friction: must be finite and >= 0");
+    REQUIRE(std::isfinite(d.elasticity[c]) && d.elasticity[c] >= 0.f, "elasticity: must be finite and >= 0");
+  }
+  auto capsule_local = [&](int c, double* e0, double* e1) {
+    double q[4] = {d.col_rot[4 * c], d.col_rot[4 * c + 1], d.col_rot[4 * c + 2], d.col_rot[4 * c + 3]};
+    dq_normalize(q);
+    const double ez[3] = {0, 0, 1};
+    double ax[3];
+    dq_rotate(q, ez, ax);
+    const double hs = std::max(0.5 * (double)d.length[c] - (double)d.radius[c], 0.0);
+    for (int i = 0; i < 3; ++i) {
+      e0[i] = d.col_pos[3 * c + i] - hs * ax[i];
+      e1[i] = d.col_pos[3 * c + i] + hs * ax[i];
+    }
+    return hs;
+  };
+  // pairs
+  std::vector<PairP> pairs;
+  for (int k = 0; k < P; ++k) {
+    int ca = d.pair_a[k], cb = d.pair_b[k];
+    REQUIRE(ca >= 0 && ca < C && cb >= 0 && cb < C && ca != cb, "pair: collider index out of range");
+    if (d.col_type[ca] == BRAX_PLANE || (d.col_type[ca] == BRAX_BOX && d.col_type[cb] == BRAX_CAPSULE))
+      std::swap(ca, cb);
+    const int ta = d.col_type[ca], tb = d.col_type[cb];
+    const float mu = d.friction[ca] * d.friction[cb];
+    const float el = d.elasticity[ca] * d.elasticity[cb];
+    REQUIRE(ta != BRAX_PLANE, "pair: plane against plane");
+    const int ba = d.col_body[ca];
+    if (tb == BRAX_PLANE) {
+      BodyP& bp = bodies[ba];
+      auto add_point = [&](const double* o, double r) {
+        REQUIRE(bp.n_points < BRAX_MAX_POINTS, "body: more than BRAX_MAX_POINTS plane-contact points");
+        PointP& pt = bp.pt[bp.n_points++];
+        for (int i = 0; i < 3; ++i) pt.o[i] = (float)o[i];
+        pt.r = (float)r;
+        pt.mu = mu;
+        pt.e = el;
+        pt.plane = plane_slot[cb];
+        pt.pad = 0;
+      };
+      if (ta == BRAX_CAPSULE) {
+        double e0[3], e1[3];
+        double hs = capsule_local(ca, e0, e1);
+        add_point(e0, d.radius[ca]);
+        if (hs > 0.0) add_point(e1, d.radius[ca]);
+      } else {
+        double q[4] = {d.col_rot[4 * ca], d.col_rot[4 * ca + 1], d.col_rot[4 * ca + 2], d.col_rot[4 * ca + 3]};
+        dq_normalize(q);
+        const float* he = d.half_extents + 3 * ca;
+        for (int m = 0; m < 8; ++m) {
+          double cl[3] = {(m & 1) ? he[0] : -he[0], (m & 2) ? he[1] : -he[1], (m & 4) ? he[2] : -he[2]};
+          double cr[3], co[3];
+          dq_rotate(q, cl, cr);
+          for (int i = 0; i < 3; ++i) co[i] = d.col_pos[3 * ca + i] + cr[i];
+          add_point(co, 0.0);
+        }
+      }
+    } else {
+      REQUIRE(ta == BRAX_CAPSULE, "pair: box-box pairs are not supported");
+      const int bb = d.col_body[cb];
+      REQUIRE(ba != bb, "pair: both colliders on one body");
+      REQUIRE((int)pairs.size() < Pb_max, "more than BRAX_MAX_PAIRS body-body pairs");
+      PairP pr;
+      std::memset(&pr, 0, sizeof(pr));
+      pr.type = tb == BRAX_CAPSULE ? kCapsuleCapsule : kCapsuleBox;
+      pr.ba = ba;
+      pr.bb = bb;
+      pr.mu = mu;
+      pr.e = el;
+      pr.ra = d.radius[ca];
+      double a0[3], a1[3];
+      capsule_local(ca, a0, a1);
+      for (int i = 0; i < 3; ++i) {
+        pr.a0[i] = (float)a0[i];
+        pr.a1[i] = (float)a1[i];
+      }
+      if (tb == BRAX_CAPSULE) {
+        double b0[3], b1[3];
+        capsule_local(cb, b0, b1);
+        pr.rb = d.radius[cb];
+        for (int i = 0; i < 3; ++i) {
+          pr.b0[i] = (float)b0[i];
+          pr.b1[i] = (float)b1[i];
+        }
+      } else {
+        double q[4] = {d.col_rot[4 * cb], d.col_rot[4 * cb + 1], d.col_rot[4 * cb + 2], d.col_rot[4 * cb + 3]};
+        dq_normalize(q);
+        double R[3][3];
+        dq_matrix(q, R);
+        for (int i = 0; i < 3; ++i) {
+          pr.b0[i] = d.col_pos[3 * cb + i];
+          pr.b1[i] = d.half_extents[3 * cb + i];
+          for (int j = 0; j < 3; ++j) pr.bR[3 * i + j] = (float)R[i][j];
+        }
+      }
+      const int idx = (int)pairs.size();
+      pairs.push_back(pr);
+      for (int side = 0; side < 2; ++side) {
+        BodyP& bp = bodies[side == 0 ? ba : bb];
+        REQUIRE(bp.n_bpairs < BRAX_MAX_BODY_PAIRS, "body: more than BRAX_MAX_BODY_PAIRS body-body pairs");
+        bp.bpair[bp.n_bpairs++] = (idx << 1) | side;
+        bp.flags |= kPublish;
+      }
+    }
+  }
+  const int Pb = (int)pairs.size();
+  S.B = B;
+  S.J = J;
+  S.A = A;
+  S.D = D;
+  S.P = Pb;
+  S.n_planes = (int)planes.size();
+  S.substeps = d.substeps;
+  S.average = d.average_contacts ? 1 : 0;
+  const double h = (double)d.dt / d.substeps;
+  S.h = (float)h;
+  S.beta_h = (float)(d.baumgarte / h);
+  S.eps = d.contact_eps;
+  for (int i = 0; i < 3; ++i) S.g[i] = d.gravity[i];
+
+  std::vector<unsigned char> blob(blob_bytes(B, Pb, S.n_planes), 0);
+  std::memcpy(blob.data(), &S, sizeof(SysP));
+  std::memcpy(blob.data() + blob_bodies_off(), bodies.data(), sizeof(BodyP) * B);
+  if (Pb) std::memcpy(blob.data() + blob_pairs_off(B), pairs.data(), sizeof(PairP) * Pb);
+  if (!planes.empty()) std::memcpy(blob.data() + blob_planes_off(B, Pb), planes.data(), sizeof(PlaneP) * planes.size());
+  *n_planes_out = S.n_planes;
+  *P_out = Pb;
+  return blob;
+}
+
+}  // namespace
+
+struct brax_system {
+  int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
+  std::vector<unsigned char> blob;
+  unsigned char* d_blob = nullptr;
+  int32_t* d_status = nullptr;
+  int groups = 1;   // groups of 32 environments per thread block
+  int variant = 0;  // launch-bounds variant of the rollout kernel
+};
+
+struct brax_batch {
+  std::vector<const brax_system*> sys;
+  std::vector<int64_t> n_envs;
+  int warps = 0;  // warps per thread block
+};
+
+namespace {
+
+size_t group_bytes(const brax_system* s) { return (size_t)group_floats(s->B, s->P) * sizeof(float); }
+
+int pick_variant(int threads) {
+  for (int v = 0; v < 3; ++v)
+    if (threads <= rollout_variant_max_threads(v)) return v;
+  return -1;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
+  Seg sg;
+  std::memset(&sg, 0, sizeof(sg));
+  sg.blob = s->d_blob;
+  sg.blob_bytes = (int32_t)s->blob.size();
+  sg.B = s->B;
+  sg.P = s->P;
+  sg.A = s->A;
+  sg.groups = groups;
+  sg.n_envs = n_envs;
+  sg.status = s->d_status;
+  return sg;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* brax_last_error(void) { return g_err.c_str(); }
+
+int brax_system_create(const brax_desc* desc, brax_system** out) {
+  if (!desc || !out) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_create: null argument");
+  *out = nullptr;
+  brax_system* s = new brax_system();
+  try {
+    s->blob = build_blob(*desc, &s->n_planes, &s->P);
+  } catch (const Rejected& r) {
+    delete s;
+    return fail(BRAX_ERR_INVALID_DESCRIPTOR, "brax_system_create: " + r.msg);
+  }
+  const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
+  s->B = S->B;
+  s->A = S->A;
+  s->D = S->D;
+  cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size());
+  if (e != cudaSuccess) {
+    delete s;
+    return e == cudaErrorMemoryAllocation ? fail(BRAX_ERR_OUT_OF_MEMORY, "brax_system_create: cudaMalloc")
+                                          : cuda_fail(e, "brax_system_create");
+  }
+  e = cudaMalloc(&s->d_status, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_blob, s->blob.data(), s->blob.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaFree(s->d_blob);
+    if (s->d_status) cudaFree(s->d_status);
+    delete s;
+    return cuda_fail(e, "brax_system_create");
+  }
+  s->groups = 1;
+  s->variant = pick_variant(32 * s->B);
+  *out = s;
+  return BRAX_OK;
+}
+
+void brax_system_destroy(brax_system* s) {
+  if (!s) return;
+  cudaFree(s->d_blob);
+  cudaFree(s->d_status);
+  delete s;
+}
+
+int brax_system_info(const brax_system* s, int32_t* n_bodies, int32_t* n_actuators, int32_t* n_dof) {
+  if (!s) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_info: null system");
+  if (n_bodies) *n_bodies = s->B;
+  if (n_actuators) *n_actuators = s->A;
+  if (n_dof) *n_dof = s->D;
+  return BRAX_OK;
+}
+
+// Launch configuration override (groups of 32 environments per block,
+// launch-bounds variant); used by the autotuner.  Not part of brax.h's
+// stable surface.
+int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant) {
+  if (!s || groups < 1 || groups > 15 || variant < 0 || variant > 2)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_launch: bad arguments");
+  if (32 * s->B * groups > rollout_variant_max_threads(variant))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_launch: block too large for the variant");
+  s->groups = groups;
+  s->variant = variant;
+  return BRAX_OK;
+}
+
+int brax_default_qp(const brax_system* s, int64_t n_envs, const float* root_pos, const float* root_rot,
+                    const float* joint_angles, float* state_out, void* stream) {
+  if (!s || !state_out || n_envs < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_default_qp: bad arguments");
+  cudaError_t e = launch_default_qp(s->d_blob, n_envs, root_pos, root_rot, joint_angles, state_out, as_stream(stream));
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_default_qp");
+}
+
+int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                 const float* actions, float* state_T, float* checkpoints, float* torso_traj, int32_t* contact_count,
+                 void* stream) {
+  if (!s || n_envs < 0 || T < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: bad arguments");
+  if (n_envs > 0 && (!state0 || !state_T || (T > 0 && s->A > 0 && !actions)))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: null state or actions");
+  if (checkpoints && K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: K must be >= 1");
+  if (n_envs == 0) return BRAX_OK;
+  if (s->variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: system too large for one block");
+  Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_segs = 1;
+  L.T = T;
+  L.K = K < 1 ? 1 : K;
+  Seg sg = make_seg(s, s->groups, n_envs);
+  const int64_t per_cta = 32LL * s->groups;
+  const int64_t grid = (n_envs + per_cta - 1) / per_cta;
+  if (grid > 0x7fffffff) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: too many environments");
+  sg.cta_begin = 0;
+  sg.cta_end = (int32_t)grid;
+  sg.state0 = state0;
+  sg.actions = actions;
+  sg.state_T = state_T;
+  sg.ckpt = checkpoints;
+  sg.torso = torso_traj;
+  sg.ccount = contact_count;
+  L.seg[0] = sg;
+  const size_t smem = s->blob.size() + s->groups * group_bytes(s);
+  cudaError_t e = launch_rollout(L, (int)grid, 32 * s->B * s->groups, smem, s->variant, as_stream(stream));
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
+}
+
+int brax_step(const brax_system* s, int64_t n_envs, const float* state_in, const float* actions, float* state_out,
+              void* stream) {
+  return brax_rollout(s, n_envs, 1, 1, state_in, actions, state_out, nullptr, nullptr, nullptr, stream);
+}
+
+int brax_sync_status(const brax_system* s, void* stream) {
+  if (!s) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_sync_status: null system");
+  cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "brax_sync_status");
+  int32_t h = 0;
+  e = cudaMemcpy(&h, s->d_status, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h) e = cudaMemset(s->d_status, 0, sizeof(int32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "brax_sync_status");
+  if (h) return fail(BRAX_ERR_NONFINITE, "brax_sync_status: a kernel produced a non-finite state");
+  return BRAX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ heterogeneous batch
+namespace {
+// Groups per block for system s when a block has `warps` warps.
+int batch_groups(const brax_system* s, int warps) { return std::max(1, std::min(15, warps / s->B)); }
+}  // namespace
+
+extern "C" {
+
+int brax_batch_create(const brax_system* const* systems, const int64_t* n_envs, int32_t n, brax_batch** out) {
+  if (!systems || !n_envs || !out || n < 1 || n > BRAX_MAX_SEGS)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_create: need 1..BRAX_MAX_SEGS systems");
+  *out = nullptr;
+  brax_batch* b = new brax_batch();
+  int warps = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!systems[i] || n_envs[i] < 0) {
+      delete b;
+      return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_create: null system or negative size");
+    }
+    b->sys.push_back(systems[i]);
+    b->n_envs.push_back(n_envs[i]);
+    warps = std::max(warps, systems[i]->B);
+  }
+  // a block holds one group of the largest system; smaller systems pack
+  // several groups of 32 environments into the same block
+  b->warps = warps;
+  *out = b;
+  return BRAX_OK;
+}
+
+void brax_batch_destroy(brax_batch* b) { delete b; }
+
+int brax_batch_offsets(const brax_batch* b, int32_t T, int32_t K, int32_t i, int64_t* state_off, int64_t* action_off,
+                       int64_t* torso_off, int64_t* ckpt_off) {
+  if (!b || i < 0 || i >= (int)b->sys.size() || T < 0 || K < 1)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_offsets: bad arguments");
+  int64_t so = 0, ao = 0, to = 0, co = 0;
+  const int64_t nck = (T + K - 1) / K;
+  for (int k = 0; k < i; ++k) {
+    const int64_t N = b->n_envs[k];
+    so += N * b->sys[k]->B * 13;
+    ao += (int64_t)T * N * b->sys[k]->A;
+    to += (int64_t)T * N * 3;
+    co += nck * N * b->sys[k]->B * 13;
+  }
+  if (state_off) *state_off = so;
+  if (action_off) *action_off = ao;
+  if (torso_off) *torso_off = to;
+  if (ckpt_off) *ckpt_off = co;
+  return BRAX_OK;
+}
+
+}  // extern "C"
+
+namespace brax_batch_impl {
+// Fill a launch table for the batch; pointers offset per system.
+int make_launch(const brax_batch* b, int32_t T, int32_t K, Launch& L, int* grid, int* threads, size_t* smem) {
+  std::memset(&L, 0, sizeof(L));
+  L.n_segs = (int)b->sys.size();
+  L.T = T;
+  L.K = K;
+  int cta = 0;
+  size_t sm = 0;
+  for (int i = 0; i < L.n_segs; ++i) {
+    const brax_system* s = b->sys[i];
+    const int G = batch_groups(s, b->warps);
+    Seg sg = make_seg(s, G, b->n_envs[i]);
+    const int64_t per = 32LL * G;
+    const int64_t nb = (b->n_envs[i] + per - 1) / per;
+    sg.cta_begin = cta;
+    sg.cta_end = cta + (int)nb;
+    cta += (int)nb;
+    sm = std::max(sm, s->blob.size() + (size_t)G * group_bytes(s));
+    L.seg[i] = sg;
+  }
+  *grid = cta;
+  *threads = 32 * b->warps;
+  *smem = sm;
+  return BRAX_OK;
+}
+}  // namespace brax_batch_impl
+
+extern "C" int brax_batch_rollout(const brax_batch* b, int32_t T, int32_t K, const float* state0, const float* actions,
+                                  float* state_T, float* checkpoints, float* torso_traj, void* stream) {
+  if (!b || T < 0 || !state0 || !state_T || (checkpoints && K < 1))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout: bad arguments");
+  if (K < 1) K = 1;
+  Launch L;
+  int grid, threads;
+  size_t smem;
+  brax_batch_impl::make_launch(b, T, K, L, &grid, &threads, &smem);
+  for (int i = 0; i < L.n_segs; ++i) {
+    int64_t so, ao, to, co;
+    brax_batch_offsets(b, T, K, i, &so, &ao, &to, &co);
+    L.seg[i].state0 = state0 + so;
+    L.seg[i].actions = actions ? actions + ao : nullptr;
+    L.seg[i].state_T = state_T + so;
+    L.seg[i].ckpt = checkpoints ? checkpoints + co : nullptr;
+    L.seg[i].torso = torso_traj ? torso_traj + to : nullptr;
+  }
+  if (grid == 0) return BRAX_OK;
+  const int variant = pick_variant(threads);
+  if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout: block too large");
+  cudaError_t e = launch_rollout(L, grid, threads, smem, variant, as_stream(stream));
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout");
+}

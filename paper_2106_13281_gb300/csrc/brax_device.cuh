@@ -1,0 +1,151 @@
+// Device helpers of the batched step: small vector algebra, shared-memory
+// layout of a group of 32 environments, and the launch table.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "brax_params.h"
+
+namespace brax {
+
+#define BRAX_MAX_SEGS 8
+
+// One system's share of a launch.  A thread block runs G groups of 32
+// environments of one system; group g's warps are bodies 0..B-1 (warp =
+// body, lane = environment).
+struct Seg {
+  const unsigned char* blob;
+  int32_t blob_bytes;
+  int32_t B, P, A;
+  int32_t groups;  // groups of 32 environments per thread block
+  int32_t cta_begin, cta_end;
+  int64_t n_envs;
+  const float* state0;
+  const float* actions;
+  float* state_T;
+  float* ckpt;
+  float* torso;
+  int32_t* ccount;
+  int32_t* status;
+  // backward
+  const float* g_state_T;
+  const float* g_torso;
+  float* g_actions;
+  float* g_state0;
+  float* ws;  // per-segment workspace
+};
+
+struct Launch {
+  int32_t n_segs;
+  int32_t T, K;
+  int32_t pad;
+  Seg seg[BRAX_MAX_SEGS];
+};
+
+// ------------------------------------------------------------------ algebra
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 mk3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 fma3(float s, V3 a, V3 b) {  // s*a + b
+  return V3{fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)};
+}
+__device__ __forceinline__ V3 ld3(const float* p) { return V3{p[0], p[1], p[2]}; }
+
+// Row-major 3x3.
+struct M3 {
+  float m[9];
+};
+__device__ __forceinline__ V3 mul(const M3& R, V3 o) {
+  return V3{fmaf(R.m[0], o.x, fmaf(R.m[1], o.y, R.m[2] * o.z)), fmaf(R.m[3], o.x, fmaf(R.m[4], o.y, R.m[5] * o.z)),
+            fmaf(R.m[6], o.x, fmaf(R.m[7], o.y, R.m[8] * o.z))};
+}
+__device__ __forceinline__ V3 mulT(const M3& R, V3 o) {
+  return V3{fmaf(R.m[0], o.x, fmaf(R.m[3], o.y, R.m[6] * o.z)), fmaf(R.m[1], o.x, fmaf(R.m[4], o.y, R.m[7] * o.z)),
+            fmaf(R.m[2], o.x, fmaf(R.m[5], o.y, R.m[8] * o.z))};
+}
+__device__ __forceinline__ V3 mulc(const M3& R, const float* o) { return mul(R, ld3(o)); }
+
+// Rotation matrix of a unit quaternion (w, x, y, z), body to world.
+__device__ __forceinline__ M3 qmat(float qw, float qx, float qy, float qz) {
+  const float xx = qx * qx, yy = qy * qy, zz = qz * qz;
+  const float xy = qx * qy, xz = qx * qz, yz = qy * qz;
+  const float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+  M3 R;
+  R.m[0] = 1.f - 2.f * (yy + zz);
+  R.m[1] = 2.f * (xy - wz);
+  R.m[2] = 2.f * (xz + wy);
+  R.m[3] = 2.f * (xy + wz);
+  R.m[4] = 1.f - 2.f * (xx + zz);
+  R.m[5] = 2.f * (yz - wx);
+  R.m[6] = 2.f * (xz - wy);
+  R.m[7] = 2.f * (yz + wx);
+  R.m[8] = 1.f - 2.f * (xx + yy);
+  return R;
+}
+
+// Symmetric 3x3 (xx, xy, xz, yy, yz, zz): world inverse inertia R diag(d) R^T.
+struct S6 {
+  float a[6];
+};
+__device__ __forceinline__ S6 inv_inertia_world(const M3& R, const float* d) {
+  S6 s;
+  const float r00 = R.m[0] * d[0], r01 = R.m[1] * d[1], r02 = R.m[2] * d[2];
+  const float r10 = R.m[3] * d[0], r11 = R.m[4] * d[1], r12 = R.m[5] * d[2];
+  s.a[0] = fmaf(r00, R.m[0], fmaf(r01, R.m[1], r02 * R.m[2]));
+  s.a[1] = fmaf(r00, R.m[3], fmaf(r01, R.m[4], r02 * R.m[5]));
+  s.a[2] = fmaf(r00, R.m[6], fmaf(r01, R.m[7], r02 * R.m[8]));
+  s.a[3] = fmaf(r10, R.m[3], fmaf(r11, R.m[4], r12 * R.m[5]));
+  s.a[4] = fmaf(r10, R.m[6], fmaf(r11, R.m[7], r12 * R.m[8]));
+  const float r20 = R.m[6] * d[0], r21 = R.m[7] * d[1], r22 = R.m[8] * d[2];
+  s.a[5] = fmaf(r20, R.m[6], fmaf(r21, R.m[7], r22 * R.m[8]));
+  return s;
+}
+__device__ __forceinline__ V3 mul(const S6& s, V3 v) {
+  return V3{fmaf(s.a[0], v.x, fmaf(s.a[1], v.y, s.a[2] * v.z)), fmaf(s.a[1], v.x, fmaf(s.a[3], v.y, s.a[4] * v.z)),
+            fmaf(s.a[2], v.x, fmaf(s.a[4], v.y, s.a[5] * v.z))};
+}
+
+// Frozen-axis masks: bit i of `bits` freezes axis i.
+__device__ __forceinline__ V3 mask3(uint32_t bits, V3 a) {
+  return V3{(bits & 1u) ? 0.f : a.x, (bits & 2u) ? 0.f : a.y, (bits & 4u) ? 0.f : a.z};
+}
+
+__device__ __forceinline__ float clamp1(float a) { return fminf(fmaxf(a, -1.f), 1.f); }
+
+// Named barrier for one group of warps (id 1..15; id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ------------------------------------------------------------------ group shared memory
+// pub  [B][24][32]: a publishing body's post-kinematic x, R, v, w and Ii
+// react[B][6][32]:  a child's joint reaction on its parent (F, tau)
+// slot [P][8][32]:  a body-body pair's impulse J, contact point p, active flag
+struct GroupMem {
+  float* pub;
+  float* react;
+  float* slot;
+  int* cnt;
+  __device__ __forceinline__ float* pubf(int b, int f) { return pub + (b * kPubFields + f) * 32; }
+  __device__ __forceinline__ float* reactf(int b, int f) { return react + (b * 6 + f) * 32; }
+  __device__ __forceinline__ float* slotf(int k, int f) { return slot + (k * 8 + f) * 32; }
+};
+__device__ __forceinline__ GroupMem group_mem(float* base, int B, int P) {
+  GroupMem m;
+  m.pub = base;
+  m.react = base + B * kPubFields * 32;
+  m.slot = m.react + B * 6 * 32;
+  m.cnt = (int*)(m.slot + P * 8 * 32);
+  return m;
+}
+
+}  // namespace brax

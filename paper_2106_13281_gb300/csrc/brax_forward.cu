@@ -1,0 +1,238 @@
+// Forward kernels: persistent rollout (also used for a single step) and
+// default_qp.
+//
+// Mapping: a thread block holds G groups of 32 environments of one system;
+// in a group, warp b is body b and lane i is environment i.  A thread keeps
+// its body's 13-float state in registers for the whole rollout; only the
+// actions stream in from HBM (three loads per step at most, reused over the
+// step's substeps).  Within a substep the warps of a group exchange the
+// parent state, joint reactions and pair impulses through shared memory at
+// two named barriers (see brax_physics.cuh).  Every warp is uniform in its
+// body role, so the only divergence is data-dependent (limits, contacts).
+#include "brax_kernels.h"
+#include "brax_physics.cuh"
+
+namespace brax {
+
+__device__ __forceinline__ void load_body(const float* p, Body& s) {
+  s.x = mk3(p[0], p[1], p[2]);
+  s.qw = p[3];
+  s.qx = p[4];
+  s.qy = p[5];
+  s.qz = p[6];
+  s.v = mk3(p[7], p[8], p[9]);
+  s.w = mk3(p[10], p[11], p[12]);
+}
+__device__ __forceinline__ void store_body(float* p, const Body& s) {
+  p[0] = s.x.x;
+  p[1] = s.x.y;
+  p[2] = s.x.z;
+  p[3] = s.qw;
+  p[4] = s.qx;
+  p[5] = s.qy;
+  p[6] = s.qz;
+  p[7] = s.v.x;
+  p[8] = s.v.y;
+  p[9] = s.v.z;
+  p[10] = s.w.x;
+  p[11] = s.w.y;
+  p[12] = s.w.z;
+}
+__device__ __forceinline__ bool body_finite(const Body& s) {
+  const float t = s.x.x + s.x.y + s.x.z + s.qw + s.qx + s.qy + s.qz + s.v.x + s.v.y + s.v.z + s.w.x + s.w.y + s.w.z;
+  return fabsf(t) < INFINITY;
+}
+
+// One substep of one (body, environment) thread; returns the number of
+// contacts this thread counted (own plane contacts + owned pairs).
+__device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodies, const PairP* pairs,
+                                               const PlaneP* planes, const BodyP& bp, int b, int B, int lane,
+                                               GroupMem& gm, int bar, int nthr, Body& s, const float* act) {
+  kinematic(bp, S.h, s);
+  const Frame f = make_frame(bp, s);
+  if (bp.flags & kPublish) publish(gm, b, lane, s, f);
+  group_sync(bar, nthr);
+  Wrench wr{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f)};
+  if (bp.flags & kHasParent) {
+    const Pub pp = read_pub(gm, bp.parent, lane);
+    wr = joint_forward(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
+  }
+  Acc acc{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f), 0};
+  for (int i = 0; i < bp.n_points; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  int counted = acc.n;
+  for (int k = b; k < S.P; k += B) counted += pair_forward(S, bodies, pairs[k], gm, k, lane);
+  group_sync(bar, nthr);
+  integrate(S, bp, gm, lane, s, f, wr, acc);
+  return counted;
+}
+
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_constant__ Launch L) {
+  int si = 0;
+  while (si + 1 < L.n_segs && (int)blockIdx.x >= L.seg[si].cta_end) ++si;
+  const Seg& sg = L.seg[si];
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (int i = threadIdx.x; i < sg.blob_bytes / 16; i += blockDim.x)
+    reinterpret_cast<int4*>(smem)[i] = reinterpret_cast<const int4*>(sg.blob)[i];
+  __syncthreads();
+  const SysP& S = *reinterpret_cast<const SysP*>(smem);
+  const BodyP* bodies = reinterpret_cast<const BodyP*>(smem + blob_bodies_off());
+  const PairP* pairs = reinterpret_cast<const PairP*>(smem + blob_pairs_off(S.B));
+  const PlaneP* planes = reinterpret_cast<const PlaneP*>(smem + blob_planes_off(S.B, S.P));
+  const int B = S.B;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / B, b = warp - g * B;
+  if (g >= sg.groups) return;  // spare warps take no part in the group barriers
+  const int64_t N = sg.n_envs;
+  const int64_t env = ((int64_t)(blockIdx.x - sg.cta_begin) * sg.groups + g) * 32 + lane;
+  const bool valid = env < N;
+  GroupMem gm = group_mem(reinterpret_cast<float*>(smem + sg.blob_bytes) + g * group_floats(B, S.P), B, S.P);
+  const int bar = 1 + g, nthr = 32 * B;
+  const BodyP& bp = bodies[b];
+  if (b == 0) gm.cnt[lane] = 0;
+  if (sg.ccount) group_sync(bar, nthr);
+
+  Body s;
+  if (valid) {
+    load_body(sg.state0 + (env * B + b) * 13, s);
+  } else {  // padding lanes step a resting body and write nothing
+    s.x = ld3(bp.rest_pos);
+    s.qw = bp.rest_rot[0];
+    s.qx = bp.rest_rot[1];
+    s.qy = bp.rest_rot[2];
+    s.qz = bp.rest_rot[3];
+    s.v = mk3(0.f, 0.f, 0.f);
+    s.w = mk3(0.f, 0.f, 0.f);
+  }
+  const int T = L.T, K = L.K, A = sg.A;
+  const int nsub = S.substeps;
+  int ccount = 0;
+  bool bad = false;
+  float act[3] = {0.f, 0.f, 0.f};
+  for (int t = 0; t < T; ++t) {
+    if (sg.ckpt && valid && (t % K) == 0) store_body(sg.ckpt + (((int64_t)(t / K) * N + env) * B + b) * 13, s);
+    if (valid && (bp.flags & kHasParent)) {
+      const float* ap = sg.actions + ((int64_t)t * N + env) * A;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
+    }
+    for (int k = 0; k < nsub; ++k)
+      ccount += substep_forward(S, bodies, pairs, planes, bp, b, B, lane, gm, bar, nthr, s, act);
+    if (sg.torso && b == 0 && valid) {
+      float* tp = sg.torso + ((int64_t)t * N + env) * 3;
+      tp[0] = s.x.x;
+      tp[1] = s.x.y;
+      tp[2] = s.x.z;
+    }
+    bad |= !body_finite(s);
+  }
+  if (valid) store_body(sg.state_T + (env * B + b) * 13, s);
+  if (bad && valid) atomicOr(sg.status, 1);
+  if (sg.ccount) {
+    atomicAdd(&gm.cnt[lane], ccount);
+    group_sync(bar, nthr);
+    if (b == 0 && valid) sg.ccount[env] = gm.cnt[lane];
+  }
+}
+
+// ------------------------------------------------------------------ default_qp
+__device__ __forceinline__ void qmul4(const float* a, const float* b, float* o) {
+  const float r0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  const float r1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  const float r2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  const float r3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+  o[0] = r0;
+  o[1] = r1;
+  o[2] = r2;
+  o[3] = r3;
+}
+__device__ __forceinline__ void qrot(const float* q, const float* v, float* o) {
+  const M3 R = qmat(q[0], q[1], q[2], q[3]);
+  const V3 r = mulc(R, v);
+  o[0] = r.x;
+  o[1] = r.y;
+  o[2] = r.z;
+}
+
+// One thread per environment walks the joint tree from its roots (Sec. 4.1
+// default_qp): R_c = R_p F_p Rot(angles) F_c^-1 and the child's anchor on the
+// parent's anchor.
+__global__ void default_qp_kernel(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
+                                  const float* angles, float* out) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const SysP& S = *reinterpret_cast<const SysP*>(blob);
+  const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
+  const int B = S.B;
+  float* o = out + n * B * 13;
+  for (int b = 0; b < B; ++b) {
+    float* ob = o + b * 13;
+    for (int i = 0; i < 3; ++i) ob[i] = bodies[b].rest_pos[i];
+    for (int i = 0; i < 4; ++i) ob[3 + i] = bodies[b].rest_rot[i];
+    for (int i = 7; i < 13; ++i) ob[i] = 0.f;
+  }
+  if (root_pos)
+    for (int i = 0; i < 3; ++i) o[i] = root_pos[n * 3 + i];
+  if (root_rot)
+    for (int i = 0; i < 4; ++i) o[3 + i] = root_rot[n * 4 + i];
+  for (int k = 0; k < S.n_order; ++k) {
+    const int c = S.joint_order[k];
+    const BodyP& bc = bodies[c];
+    const int p = bc.parent;
+    float qp[4] = {o[p * 13 + 3], o[p * 13 + 4], o[p * 13 + 5], o[p * 13 + 6]};
+    const float np_ = rsqrtf(qp[0] * qp[0] + qp[1] * qp[1] + qp[2] * qp[2] + qp[3] * qp[3]);
+    for (int i = 0; i < 4; ++i) qp[i] *= np_;
+    float rel[4] = {1.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < bc.dof; ++a) {
+      const float th = angles ? angles[n * S.D + bc.dof_offset + a] : 0.f;
+      float sn, cs;
+      sincosf(0.5f * th, &sn, &cs);
+      float r[4] = {cs, 0.f, 0.f, 0.f};
+      r[1 + a] = sn;
+      qmul4(rel, r, rel);
+    }
+    const float fci[4] = {bc.frame_c[0], -bc.frame_c[1], -bc.frame_c[2], -bc.frame_c[3]};
+    float qc[4];
+    qmul4(qp, bc.frame_p, qc);
+    qmul4(qc, rel, qc);
+    qmul4(qc, fci, qc);
+    const float nc = rsqrtf(qc[0] * qc[0] + qc[1] * qc[1] + qc[2] * qc[2] + qc[3] * qc[3]);
+    for (int i = 0; i < 4; ++i) qc[i] *= nc;
+    float rp[3], rc[3];
+    qrot(qp, bc.off_p, rp);
+    qrot(qc, bc.off_c, rc);
+    for (int i = 0; i < 3; ++i) o[c * 13 + i] = o[p * 13 + i] + rp[i] - rc[i];
+    for (int i = 0; i < 4; ++i) o[c * 13 + 3 + i] = qc[i];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int MAXT, int MINB>
+static cudaError_t launch_rollout_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
+  auto k = rollout_kernel<MAXT, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st) {
+  switch (variant) {
+    case 0: return launch_rollout_t<384, 2>(L, grid, threads, smem, st);
+    case 1: return launch_rollout_t<640, 1>(L, grid, threads, smem, st);
+    default: return launch_rollout_t<1024, 1>(L, grid, threads, smem, st);
+  }
+}
+
+int rollout_variant_max_threads(int variant) { return variant == 0 ? 384 : (variant == 1 ? 640 : 1024); }
+
+cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
+                              const float* angles, float* out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int64_t grid = (N + threads - 1) / threads;
+  default_qp_kernel<<<(unsigned)grid, threads, 0, st>>>(blob, N, root_pos, root_rot, angles, out);
+  return cudaGetLastError();
+}
+
+}  // namespace brax

@@ -1,0 +1,17 @@
+// Launchers of the device kernels (host side of the kernel translation units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "brax_device.cuh"
+
+namespace brax {
+
+// variant: 0 = (384 threads, 2 blocks/SM), 1 = (640, 1), 2 = (1024, 1) launch bounds
+cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+int rollout_variant_max_threads(int variant);
+cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
+                              const float* angles, float* out, cudaStream_t st);
+
+}  // namespace brax

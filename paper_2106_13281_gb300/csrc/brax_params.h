@@ -1,0 +1,110 @@
+// Device-side parameter layout of one system (host and device).
+//
+// brax_system_create flattens a validated descriptor into one blob:
+//   SysP | BodyP[B] | PairP[P] | PlaneP[n_planes]
+// which every thread block copies into shared memory before stepping.  All
+// geometry is pre-resolved to what a body's warp needs: its inverse mass and
+// inertia, its parent joint (a body is the child of at most one joint), its
+// plane-contact points (capsule end spheres, box corners) and the body-body
+// pairs it takes part in.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/brax.h"
+
+namespace brax {
+
+enum BodyFlags : uint32_t {
+  kFrozenPos0 = 1u << 0,  // bits 0..2: frozen world position axes
+  kFrozenRot0 = 1u << 3,  // bits 3..5: frozen world rotation axes
+  kAnyFrozen = 1u << 6,
+  kHasParent = 1u << 7,   // the body is the child of a joint
+  kPublish = 1u << 8,     // other warps read this body's substep state
+};
+
+// A plane-contact point of a body: a sphere of radius r centred at o (body
+// frame) tested against plane `plane`.  Capsules give their two end spheres
+// (one when the segment has zero length), boxes their eight corners (r = 0).
+struct PointP {
+  float o[3];
+  float r;
+  float mu, e;
+  int32_t plane;
+  int32_t pad;
+};
+
+struct BodyP {
+  float inv_mass;
+  float inv_I[3];
+  uint32_t flags;
+  int32_t parent;  // parent body of the joint whose child this body is, -1 if none
+  int32_t dof;     // 1 or 3
+  int32_t joint;   // that joint's index
+  float off_p[3], off_c[3];
+  float ap[9];     // joint frame axes x, y, z in the parent's body frame
+  float ac[9];     // joint frame axes x, y, z in this body's frame
+  float k, c, ka, ca, kl;
+  float lo[3], hi[3];  // radians
+  int32_t act[3];      // actuator index per joint axis, -1 none
+  float gear[3];
+  int32_t n_children;
+  int32_t children[BRAX_MAX_CHILDREN];
+  int32_t n_points;
+  PointP pt[BRAX_MAX_POINTS];
+  int32_t n_bpairs;
+  int32_t bpair[BRAX_MAX_BODY_PAIRS];  // (pair index << 1) | side; side 0: +J (body a), 1: -J (body b)
+  // default_qp: rest pose for roots
+  float rest_pos[3];
+  float rest_rot[4];
+  float frame_p[4], frame_c[4];  // joint frame quaternions (normalised)
+  int32_t dof_offset;            // first joint-angle index of the parent joint
+  int32_t pad;
+};
+
+enum PairType : int32_t { kCapsuleCapsule = 0, kCapsuleBox = 1 };
+
+// A body-body pair: capsule a (segment a0..a1 in body a's frame, radius ra)
+// against capsule b (segment b0..b1, radius rb) or against box b (centre b0,
+// half extents b1, axes bR columns, all in body b's frame).
+struct PairP {
+  int32_t type;
+  int32_t ba, bb;
+  int32_t pad;
+  float mu, e;
+  float ra, rb;
+  float a0[3], a1[3];
+  float b0[3], b1[3];
+  float bR[9];
+};
+
+struct PlaneP {
+  float p0[3];
+  float n[3];
+};
+
+struct SysP {
+  int32_t B, J, A, D, P, n_planes, substeps, average;
+  float h, beta_h, eps, pad0;  // beta_h = baumgarte / h
+  float g[3];
+  float pad1;
+  int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
+  int32_t n_order;
+  int32_t pad2[3];
+};
+
+// Byte offsets inside the blob.
+__host__ __device__ inline int blob_bodies_off() { return (int)sizeof(SysP); }
+__host__ __device__ inline int blob_pairs_off(int B) { return blob_bodies_off() + B * (int)sizeof(BodyP); }
+__host__ __device__ inline int blob_planes_off(int B, int P) { return blob_pairs_off(B) + P * (int)sizeof(PairP); }
+__host__ __device__ inline int blob_bytes(int B, int P, int n_planes) {
+  int b = blob_planes_off(B, P) + n_planes * (int)sizeof(PlaneP);
+  return (b + 15) & ~15;
+}
+
+// Shared memory of one group of 32 environments (floats), after the blob.
+constexpr int kPubFields = 24;  // x[3], R[9], v[3], w[3], Ii[6]
+__host__ __device__ inline int group_floats(int B, int P) {
+  return B * kPubFields * 32 + B * 6 * 32 + P * 8 * 32 + 32;
+}
+
+}  // namespace brax

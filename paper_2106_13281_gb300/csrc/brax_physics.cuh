@@ -1,0 +1,460 @@
+// Forward physics of one substep for one (body, environment) thread.
+//
+// A group of 32 environments runs as B warps, warp b = body b, lane = env.
+// One substep is Algorithm 1 (Sec. 3) split at two group barriers:
+//   phase K  kinematic integrator of the own body, its frame, publish;
+//   -- barrier --
+//   phase J  the parent joint and its actuators (the own body is the joint's
+//            child; the reaction on the parent goes to shared memory), the
+//            own plane contacts, the body-body pairs this warp owns;
+//   -- barrier --
+//   phase P  sum the reactions of the children and the pair impulses,
+//            potential integrator, collision integrator.
+// Joints, actuators and contacts all read the same post-kinematic state and
+// the velocities before the potential update (Algorithm 1 applies colliders
+// before the potential integrator).
+#pragma once
+#include "brax_device.cuh"
+
+namespace brax {
+
+struct Body {
+  V3 x;
+  float qw, qx, qy, qz;
+  V3 v, w;
+};
+
+struct Frame {
+  M3 R;
+  S6 Ii;
+};
+
+struct Wrench {
+  V3 F, tau;
+};
+
+struct Acc {
+  V3 dv, dw;
+  int n;
+};
+
+// ------------------------------------------------------------------ phase K
+// Kinematic integrator (Algorithm 1, first line): x += h v;
+// q <- normalize(q + h/2 (0, w) (x) q), w in world frame.  Frozen axes hold
+// zero velocity.
+__device__ __forceinline__ void kinematic(const BodyP& bp, float h, Body& s) {
+  if (bp.flags & kAnyFrozen) {
+    s.v = mask3(bp.flags, s.v);
+    s.w = mask3(bp.flags >> 3, s.w);
+  }
+  s.x = fma3(h, s.v, s.x);
+  const float hh = 0.5f * h;
+  const float nw = fmaf(-hh, fmaf(s.w.x, s.qx, fmaf(s.w.y, s.qy, s.w.z * s.qz)), s.qw);
+  const float nx = fmaf(hh, fmaf(s.qw, s.w.x, fmaf(s.w.y, s.qz, -s.w.z * s.qy)), s.qx);
+  const float ny = fmaf(hh, fmaf(s.qw, s.w.y, fmaf(s.w.z, s.qx, -s.w.x * s.qz)), s.qy);
+  const float nz = fmaf(hh, fmaf(s.qw, s.w.z, fmaf(s.w.x, s.qy, -s.w.y * s.qx)), s.qz);
+  const float inv = rsqrtf(fmaf(nw, nw, fmaf(nx, nx, fmaf(ny, ny, nz * nz))));
+  s.qw = nw * inv;
+  s.qx = nx * inv;
+  s.qy = ny * inv;
+  s.qz = nz * inv;
+}
+
+__device__ __forceinline__ Frame make_frame(const BodyP& bp, const Body& s) {
+  Frame f;
+  f.R = qmat(s.qw, s.qx, s.qy, s.qz);
+  f.Ii = inv_inertia_world(f.R, bp.inv_I);
+  return f;
+}
+
+__device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Body& s, const Frame& f) {
+  float* p = gm.pubf(b, 0) + lane;
+  p[0 * 32] = s.x.x;
+  p[1 * 32] = s.x.y;
+  p[2 * 32] = s.x.z;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) p[(3 + i) * 32] = f.R.m[i];
+  p[12 * 32] = s.v.x;
+  p[13 * 32] = s.v.y;
+  p[14 * 32] = s.v.z;
+  p[15 * 32] = s.w.x;
+  p[16 * 32] = s.w.y;
+  p[17 * 32] = s.w.z;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[(18 + i) * 32] = f.Ii.a[i];
+}
+
+struct Pub {
+  V3 x;
+  M3 R;
+  V3 v, w;
+};
+__device__ __forceinline__ Pub read_pub(GroupMem& gm, int b, int lane) {
+  const float* p = gm.pubf(b, 0) + lane;
+  Pub o;
+  o.x = mk3(p[0], p[32], p[64]);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) o.R.m[i] = p[(3 + i) * 32];
+  o.v = mk3(p[12 * 32], p[13 * 32], p[14 * 32]);
+  o.w = mk3(p[15 * 32], p[16 * 32], p[17 * 32]);
+  return o;
+}
+__device__ __forceinline__ S6 read_pub_Ii(GroupMem& gm, int b, int lane) {
+  const float* p = gm.pubf(b, 18) + lane;
+  S6 s;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) s.a[i] = p[i * 32];
+  return s;
+}
+
+// ------------------------------------------------------------------ phase J: joint
+// Spring joint (Sec. 3 joint.revolute, Sec. 7.1): anchor spring-damper F on
+// the child at its anchor and -F on the parent at its anchor; hinge-axis
+// alignment spring; angular damper (hinge: about the axis, 3-DOF: 3-D);
+// one-sided limit springs on the joint angles (App. A angle_limit); torque
+// actuators gear * clamp(a, -1, 1) about the joint axes (Sec. 3).  Returns
+// the child's wrench; writes the parent's to the react buffer.
+__device__ __forceinline__ Wrench joint_forward(const BodyP& bp, const Pub& pp, const Body& s, const Frame& f,
+                                                const float* act, float* react_out /* reactf(b,0)+lane */) {
+  const V3 rp = mulc(pp.R, bp.off_p);
+  const V3 rc = mulc(f.R, bp.off_c);
+  const V3 dpc = (pp.x + rp) - (s.x + rc);
+  const V3 up = pp.v + cross(pp.w, rp);
+  const V3 uc = s.v + cross(s.w, rc);
+  const V3 F = bp.k * dpc - bp.c * (uc - up);
+  V3 tc = cross(rc, F);
+  V3 tp = -cross(rp, F);
+  const V3 P0 = mulc(pp.R, bp.ap + 0);
+  const V3 P1 = mulc(pp.R, bp.ap + 3);
+  const V3 wr = s.w - pp.w;
+  V3 tj;
+  if (bp.dof == 1) {
+    const V3 Ac = mulc(f.R, bp.ac + 0);
+    const V3 yc = mulc(f.R, bp.ac + 3);
+    const float th = atan2f(dot(cross(P1, yc), P0), dot(P1, yc));
+    float L = 0.f;
+    if (th < bp.lo[0]) L = bp.kl * (bp.lo[0] - th);
+    else if (th > bp.hi[0]) L = bp.kl * (bp.hi[0] - th);
+    float sc = L - bp.ca * dot(wr, P0);
+    if (bp.act[0] >= 0) sc = fmaf(bp.gear[0], clamp1(act[0]), sc);
+    tj = fma3(sc, P0, bp.ka * cross(Ac, P0));
+  } else {
+    const V3 P2 = mulc(pp.R, bp.ap + 6);
+    const V3 C0 = mulc(f.R, bp.ac + 0);
+    const V3 C1 = mulc(f.R, bp.ac + 3);
+    const V3 C2 = mulc(f.R, bp.ac + 6);
+    const float m00 = dot(P0, C0), m01 = dot(P0, C1), m02 = dot(P0, C2);
+    const float m12 = dot(P1, C2), m22 = dot(P2, C2);
+    float th[3];
+    th[0] = atan2f(-m12, m22);
+    th[1] = atan2f(m02, sqrtf(fmaf(m00, m00, m01 * m01)));
+    th[2] = atan2f(-m01, m00);
+    tj = -bp.ca * wr;
+    const V3 Pk[3] = {P0, P1, P2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float L = 0.f;
+      if (th[a] < bp.lo[a]) L = bp.kl * (bp.lo[a] - th[a]);
+      else if (th[a] > bp.hi[a]) L = bp.kl * (bp.hi[a] - th[a]);
+      if (bp.act[a] >= 0) L = fmaf(bp.gear[a], clamp1(act[a]), L);
+      tj = fma3(L, Pk[a], tj);
+    }
+  }
+  tc = tc + tj;
+  tp = tp - tj;
+  react_out[0 * 32] = -F.x;
+  react_out[1 * 32] = -F.y;
+  react_out[2 * 32] = -F.z;
+  react_out[3 * 32] = tp.x;
+  react_out[4 * 32] = tp.y;
+  react_out[5 * 32] = tp.z;
+  return Wrench{F, tc};
+}
+
+// ------------------------------------------------------------------ phase J: contacts
+// Velocity change at a body's contact point along `dir` per unit impulse
+// along `dir` (frozen axes excluded).
+__device__ __forceinline__ float eff_mass(uint32_t flags, float inv_m, const S6& Ii, V3 l, V3 dir) {
+  V3 dm = dir;
+  V3 ld = cross(l, dir);
+  V3 om = mul(Ii, ld);
+  if (flags & kAnyFrozen) {
+    dm = mask3(flags, dm);
+    om = mask3(flags >> 3, om);
+  }
+  return fmaf(dot(dm, dir), inv_m, dot(om, ld));
+}
+
+// Velocity-level contact with Baumgarte stabilisation (Sec. 7.2): normal
+// impulse toward the target max(beta depth / h, -e u_n), Coulomb friction
+// against the sliding direction.  u is the relative contact velocity (a - b),
+// k_n/k_t the summed effective inverse masses.  Returns the impulse on a.
+struct Eff {
+  uint32_t flags;
+  float inv_m;
+};
+
+// Plane contact of the own body: sphere (centre R o + x, radius r).
+__device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, const PointP& pt, const PlaneP& pl,
+                                            const Body& s, const Frame& f, Acc& acc) {
+  const V3 ro = mulc(f.R, pt.o);
+  const V3 n = ld3(pl.n);
+  const float dist = dot((s.x + ro) - ld3(pl.p0), n);
+  const float depth = pt.r - dist;
+  if (!(depth > 0.f)) return;
+  const V3 l = fma3(-pt.r, n, ro);  // contact point e - r n, relative to the centre of mass
+  const V3 u = s.v + cross(s.w, l);
+  const float kn = eff_mass(bp.flags, bp.inv_mass, f.Ii, l, n);
+  if (!(kn > 0.f)) return;
+  const float un = dot(u, n);
+  const float target = fmaxf(S.beta_h * depth, -pt.e * un);
+  const float jn = fmaxf(__fdividef(target - un, kn), 0.f);
+  V3 J = jn * n;
+  const V3 ut = fma3(-un, n, u);
+  const float ut2 = dot(ut, ut);
+  if (ut2 > S.eps * S.eps) {
+    const float rinv = rsqrtf(ut2);
+    const float utn = ut2 * rinv;
+    const V3 t = rinv * ut;
+    const float kt = eff_mass(bp.flags, bp.inv_mass, f.Ii, l, t);
+    const float jt = fminf(__fdividef(utn, kt), pt.mu * jn);
+    J = fma3(-jt, t, J);
+  }
+  V3 dv = bp.inv_mass * J;
+  V3 dw = mul(f.Ii, cross(l, J));
+  if (bp.flags & kAnyFrozen) {
+    dv = mask3(bp.flags, dv);
+    dw = mask3(bp.flags >> 3, dw);
+  }
+  acc.dv = acc.dv + dv;
+  acc.dw = acc.dw + dw;
+  acc.n += 1;
+}
+
+// Closest points of segments P1 + s d1 and P2 + t d2 (s, t in [0, 1]);
+// zero-length segments reduce to points, near-parallel ones take s = 0.
+__device__ __forceinline__ void segment_closest(V3 P1, V3 d1, V3 P2, V3 d2, float& s, float& t) {
+  const V3 r = P1 - P2;
+  const float a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+  const float tiny = 1e-12f;
+  if (a <= tiny && e <= tiny) {
+    s = 0.f;
+    t = 0.f;
+    return;
+  }
+  if (a <= tiny) {
+    s = 0.f;
+    t = fminf(fmaxf(__fdividef(f, e), 0.f), 1.f);
+    return;
+  }
+  const float c = dot(d1, r);
+  if (e <= tiny) {
+    t = 0.f;
+    s = fminf(fmaxf(__fdividef(-c, a), 0.f), 1.f);
+    return;
+  }
+  const float b = dot(d1, d2);
+  const float ae = a * e;
+  const float denom = ae - b * b;
+  s = (denom > 1e-5f * ae) ? fminf(fmaxf(__fdividef(fmaf(b, f, -c * e), denom), 0.f), 1.f) : 0.f;
+  t = __fdividef(fmaf(b, s, f), e);
+  if (t < 0.f) {
+    t = 0.f;
+    s = fminf(fmaxf(__fdividef(-c, a), 0.f), 1.f);
+  } else if (t > 1.f) {
+    t = 1.f;
+    s = fminf(fmaxf(__fdividef(b - c, a), 0.f), 1.f);
+  }
+}
+
+// Squared distance from a box-frame point to the box.
+__device__ __forceinline__ float box_d2(V3 e, const float* he) {
+  const float dx = e.x - fminf(fmaxf(e.x, -he[0]), he[0]);
+  const float dy = e.y - fminf(fmaxf(e.y, -he[1]), he[1]);
+  const float dz = e.z - fminf(fmaxf(e.z, -he[2]), he[2]);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Golden-section minimisation of the segment-box distance over the segment
+// parameter (24 iterations, one new evaluation each).
+__device__ __forceinline__ float seg_box_param(V3 Pl, V3 dl, const float* he) {
+  const float rho = 0.6180339887498949f;
+  float a = 0.f, b = 1.f;
+  float c = b - rho * (b - a), d = a + rho * (b - a);
+  float fc = box_d2(fma3(c, dl, Pl), he), fd = box_d2(fma3(d, dl, Pl), he);
+  for (int it = 0; it < 24; ++it) {
+    if (fc < fd) {
+      b = d;
+      d = c;
+      fd = fc;
+      c = b - rho * (b - a);
+      fc = box_d2(fma3(c, dl, Pl), he);
+    } else {
+      a = c;
+      c = d;
+      fc = fd;
+      d = a + rho * (b - a);
+      fd = box_d2(fma3(d, dl, Pl), he);
+    }
+  }
+  return 0.5f * (a + b);
+}
+
+// Detect one body-body pair; on contact compute the impulse on body a and
+// write (J, p, 1) to the pair's slot, else (0, 0, 0).
+__device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, const PairP& pr, GroupMem& gm,
+                                            int k, int lane) {
+  const Pub A = read_pub(gm, pr.ba, lane);
+  const Pub Bq = read_pub(gm, pr.bb, lane);
+  const V3 P1 = A.x + mulc(A.R, pr.a0);
+  const V3 d1 = mulc(A.R, pr.a1) - mulc(A.R, pr.a0);
+  V3 n, p;
+  float depth;
+  bool hit = false;
+  if (pr.type == kCapsuleCapsule) {
+    const V3 P2 = Bq.x + mulc(Bq.R, pr.b0);
+    const V3 d2 = mulc(Bq.R, pr.b1) - mulc(Bq.R, pr.b0);
+    float sp, tp;
+    segment_closest(P1, d1, P2, d2, sp, tp);
+    const V3 c1 = fma3(sp, d1, P1), c2 = fma3(tp, d2, P2);
+    const V3 df = c1 - c2;
+    const float dl2 = dot(df, df);
+    const float dl = sqrtf(dl2);
+    depth = pr.ra + pr.rb - dl;
+    if (dl >= S.eps && depth > 0.f) {
+      const float inv = __fdividef(1.f, dl);
+      n = inv * df;
+      p = 0.5f * (fma3(-pr.ra, n, c1) + fma3(pr.rb, n, c2));
+      hit = true;
+    }
+  } else {
+    // box frame: rotation Rb = R_b * bR, centre cb
+    M3 Rb;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Rb.m[3 * i + j] = fmaf(Bq.R.m[3 * i + 0], pr.bR[0 * 3 + j],
+                               fmaf(Bq.R.m[3 * i + 1], pr.bR[1 * 3 + j], Bq.R.m[3 * i + 2] * pr.bR[2 * 3 + j]));
+    const V3 cb = Bq.x + mulc(Bq.R, pr.b0);
+    const V3 Pl = mulT(Rb, P1 - cb);
+    const V3 dl = mulT(Rb, d1);
+    const float* he = pr.b1;
+    const float t = seg_box_param(Pl, dl, he);
+    const V3 e = fma3(t, dl, Pl);
+    const V3 q = mk3(fminf(fmaxf(e.x, -he[0]), he[0]), fminf(fmaxf(e.y, -he[1]), he[1]),
+                     fminf(fmaxf(e.z, -he[2]), he[2]));
+    const V3 dv = e - q;
+    const float d2 = dot(dv, dv);
+    V3 nl, pl;
+    if (d2 > 1e-12f) {
+      const float dist = sqrtf(d2);
+      const float inv = __fdividef(1.f, dist);
+      nl = inv * dv;
+      depth = pr.ra - dist;
+      pl = 0.5f * (fma3(-pr.ra, nl, e) + q);
+    } else {
+      const float px = he[0] - fabsf(e.x), py = he[1] - fabsf(e.y), pz = he[2] - fabsf(e.z);
+      int kk = 0;
+      float pen = px;
+      if (py < pen) { pen = py; kk = 1; }
+      if (pz < pen) { pen = pz; kk = 2; }
+      const float ek = kk == 0 ? e.x : (kk == 1 ? e.y : e.z);
+      const float sg = ek >= 0.f ? 1.f : -1.f;
+      nl = mk3(kk == 0 ? sg : 0.f, kk == 1 ? sg : 0.f, kk == 2 ? sg : 0.f);
+      depth = pr.ra + pen;
+      pl = fma3(0.5f * (pen - pr.ra), nl, e);
+    }
+    if (depth > 0.f) {
+      n = mul(Rb, nl);
+      p = cb + mul(Rb, pl);
+      hit = true;
+    }
+  }
+  float* sl = gm.slotf(k, 0) + lane;
+  if (!hit) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) sl[i * 32] = 0.f;
+    return 0;
+  }
+  const BodyP& ba = bodies[pr.ba];
+  const BodyP& bb = bodies[pr.bb];
+  const S6 Ia = read_pub_Ii(gm, pr.ba, lane);
+  const S6 Ib = read_pub_Ii(gm, pr.bb, lane);
+  const V3 la = p - A.x, lb = p - Bq.x;
+  const V3 u = (A.v + cross(A.w, la)) - (Bq.v + cross(Bq.w, lb));
+  const float kn = eff_mass(ba.flags, ba.inv_mass, Ia, la, n) + eff_mass(bb.flags, bb.inv_mass, Ib, lb, n);
+  if (!(kn > 0.f)) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) sl[i * 32] = 0.f;
+    return 0;
+  }
+  const float un = dot(u, n);
+  const float target = fmaxf(S.beta_h * depth, -pr.e * un);
+  const float jn = fmaxf(__fdividef(target - un, kn), 0.f);
+  V3 J = jn * n;
+  const V3 ut = fma3(-un, n, u);
+  const float ut2 = dot(ut, ut);
+  if (ut2 > S.eps * S.eps) {
+    const float rinv = rsqrtf(ut2);
+    const float utn = ut2 * rinv;
+    const V3 t = rinv * ut;
+    const float kt = eff_mass(ba.flags, ba.inv_mass, Ia, la, t) + eff_mass(bb.flags, bb.inv_mass, Ib, lb, t);
+    const float jt = fminf(__fdividef(utn, kt), pr.mu * jn);
+    J = fma3(-jt, t, J);
+  }
+  sl[0 * 32] = J.x;
+  sl[1 * 32] = J.y;
+  sl[2 * 32] = J.z;
+  sl[3 * 32] = p.x;
+  sl[4 * 32] = p.y;
+  sl[5 * 32] = p.z;
+  sl[6 * 32] = 1.f;
+  return 1;
+}
+
+// ------------------------------------------------------------------ phase P
+// Potential integrator: v += h (F/m + g), w += h Ii tau; collision
+// integrator: the mean (or sum) of the contact velocity changes.
+__device__ __forceinline__ void integrate(const SysP& S, const BodyP& bp, GroupMem& gm, int lane, Body& s,
+                                          const Frame& f, Wrench wr, Acc acc) {
+  for (int c = 0; c < bp.n_children; ++c) {
+    const float* r = gm.reactf(bp.children[c], 0) + lane;
+    wr.F = wr.F + mk3(r[0], r[32], r[64]);
+    wr.tau = wr.tau + mk3(r[96], r[128], r[160]);
+  }
+  for (int i = 0; i < bp.n_bpairs; ++i) {
+    const int code = bp.bpair[i];
+    const float* sl = gm.slotf(code >> 1, 0) + lane;
+    if (sl[6 * 32] != 0.f) {
+      const float sg = (code & 1) ? -1.f : 1.f;
+      const V3 J = sg * mk3(sl[0], sl[32], sl[64]);
+      const V3 l = mk3(sl[96], sl[128], sl[160]) - s.x;
+      V3 dv = bp.inv_mass * J;
+      V3 dw = mul(f.Ii, cross(l, J));
+      if (bp.flags & kAnyFrozen) {
+        dv = mask3(bp.flags, dv);
+        dw = mask3(bp.flags >> 3, dw);
+      }
+      acc.dv = acc.dv + dv;
+      acc.dw = acc.dw + dw;
+      acc.n += 1;
+    }
+  }
+  const float h = S.h;
+  V3 v = fma3(h, fma3(bp.inv_mass, wr.F, ld3(S.g)), s.v);
+  V3 w = fma3(h, mul(f.Ii, wr.tau), s.w);
+  if (bp.flags & kAnyFrozen) {
+    v = mask3(bp.flags, v);
+    w = mask3(bp.flags >> 3, w);
+  }
+  if (acc.n > 0) {
+    const float inv = (S.average && acc.n > 1) ? __fdividef(1.f, (float)acc.n) : 1.f;
+    v = fma3(inv, acc.dv, v);
+    w = fma3(inv, acc.dw, w);
+  }
+  s.v = v;
+  s.w = w;
+}
+
+}  // namespace brax

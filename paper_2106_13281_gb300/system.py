@@ -1,0 +1,114 @@
+"""Python front end of the C ABI: systems, rollouts and their gradients on
+PyTorch CUDA tensors.  Argument marshalling only; the work runs in
+libbrax_gb300.so."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from .binding import _ptr, _stream, check, load_library, marshal_desc
+
+
+def _f32(t, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class BraxSystem:
+    """One system (Sec. 4.1 system specification) uploaded to the current GPU."""
+
+    def __init__(self, desc: dict):
+        L = load_library()
+        d, keep = marshal_desc(desc)
+        h = C.c_void_p()
+        check(L.brax_system_create(C.byref(d), C.byref(h)))
+        self._L = L
+        self._h = h
+        self.desc = desc
+        B, A, D = C.c_int32(), C.c_int32(), C.c_int32()
+        check(L.brax_system_info(h, C.byref(B), C.byref(A), C.byref(D)))
+        self.B, self.A, self.D = B.value, A.value, D.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.brax_system_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_launch(self, groups: int, variant: int):
+        check(self._L.brax_system_set_launch(self._h, groups, variant))
+
+    # ---------------------------------------------------------------- forward
+    def default_qp(self, n_envs, root_pos=None, root_rot=None, angles=None):
+        out = torch.empty((n_envs, self.B, 13), device="cuda", dtype=torch.float32)
+        check(self._L.brax_default_qp(self._h, n_envs, _ptr(_f32(root_pos, (n_envs, 3), "root_pos")),
+                                      _ptr(_f32(root_rot, (n_envs, 4), "root_rot")),
+                                      _ptr(_f32(angles, (n_envs, self.D), "angles")), _ptr(out), _stream()))
+        return out
+
+    def step(self, state, actions, out=None):
+        N = state.shape[0]
+        _f32(state, (N, self.B, 13), "state")
+        _f32(actions, (N, self.A), "actions")
+        out = torch.empty_like(state) if out is None else _f32(out, (N, self.B, 13), "out")
+        check(self._L.brax_step(self._h, N, _ptr(state), _ptr(actions), _ptr(out), _stream()))
+        return out
+
+    def rollout(self, state0, actions, K=1, checkpoints=False, torso=False, contact_count=False, state_T=None):
+        """T steps in one persistent launch.  Returns a dict with state_T and
+        the requested checkpoints [ceil(T/K),N,B,13], torso [T,N,3] and
+        contact_count [N]."""
+        N = state0.shape[0]
+        T = actions.shape[0]
+        _f32(state0, (N, self.B, 13), "state0")
+        _f32(actions, (T, N, self.A), "actions")
+        out = {"state_T": torch.empty_like(state0) if state_T is None else state_T}
+        if checkpoints:
+            out["checkpoints"] = torch.empty((math.ceil(T / K), N, self.B, 13), device="cuda", dtype=torch.float32)
+        if torso:
+            out["torso"] = torch.empty((T, N, 3), device="cuda", dtype=torch.float32)
+        if contact_count:
+            out["contact_count"] = torch.zeros((N,), device="cuda", dtype=torch.int32)
+        check(self._L.brax_rollout(self._h, N, T, K, _ptr(state0), _ptr(actions), _ptr(out["state_T"]),
+                                   _ptr(out.get("checkpoints")), _ptr(out.get("torso")),
+                                   _ptr(out.get("contact_count")), _stream()))
+        return out
+
+    # ---------------------------------------------------------------- backward
+    def workspace_size(self, n_envs, T, K):
+        b = C.c_size_t()
+        check(self._L.brax_workspace_size(self._h, n_envs, T, K, C.byref(b)))
+        return b.value
+
+    def rollout_backward(self, state0, actions, checkpoints, g_state_T, g_torso=None, K=1, workspace=None):
+        N = state0.shape[0]
+        T = actions.shape[0]
+        _f32(state0, (N, self.B, 13), "state0")
+        _f32(actions, (T, N, self.A), "actions")
+        _f32(checkpoints, (math.ceil(T / K), N, self.B, 13), "checkpoints")
+        _f32(g_state_T, (N, self.B, 13), "g_state_T")
+        _f32(g_torso, (T, N, 3), "g_torso")
+        nbytes = self.workspace_size(N, T, K)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty((max(nbytes, 1),), device="cuda", dtype=torch.uint8)
+        g_actions = torch.empty_like(actions)
+        g_state0 = torch.empty_like(state0)
+        check(self._L.brax_rollout_backward(self._h, N, T, K, _ptr(state0), _ptr(actions), _ptr(checkpoints),
+                                            _ptr(g_state_T), _ptr(g_torso), _ptr(g_actions), _ptr(g_state0),
+                                            _ptr(workspace), workspace.numel(), _stream()))
+        return g_actions, g_state0
+
+    def sync_status(self):
+        """Synchronise the current stream; raise if a kernel saw a non-finite state."""
+        check(self._L.brax_sync_status(self._h, _stream()))

@@ -1,0 +1,182 @@
+"""Parity of the CUDA forward path with the FP64 oracle (GPU).
+
+Inputs are seeded and shared; the oracle runs on the same FP32-rounded
+initial states.  Tolerances: one step <= 1e-5 m in position; 50 steps
+<= 1e-3 m; beyond the chaotic horizon the torso displacement distributions
+agree (two-sample KS test and means within 3 standard errors)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2106_13281_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def brax():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_13281_gb300.system import BraxSystem
+    return BraxSystem
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(f32(a))).cuda()
+
+
+def initial(desc, N, seed, jitter=0.0, drop=0.0):
+    rp, rr, ang = S.initial_conditions(desc, N, seed, height_jitter=jitter)
+    rp[:, 2] -= drop
+    st = orc.default_qp(desc, N, rp, rr, ang)
+    return f32(st).astype(np.float64), (rp, rr, ang)
+
+
+SCENE_CASES = [("quadruped", 0.38), ("biped", 0.0), ("pendulum", 0.0), ("arm_box", 0.0)]
+
+
+@pytest.mark.parametrize("name", [c[0] for c in SCENE_CASES])
+def test_default_qp_matches_oracle(brax, name):
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    N = 70
+    rp, rr, ang = S.initial_conditions(d, N, 1, height_jitter=0.05)
+    ref = orc.default_qp(d, N, rp, rr, ang)
+    got = sysm.default_qp(N, cuda(rp), cuda(rr), cuda(ang)).cpu().numpy()
+    assert np.abs(got - ref).max() < 2e-6
+
+
+def settled_states(d, name, N, seed, drop, T=30):
+    """States after T oracle steps (contacts, limits and joints active)."""
+    st, _ = initial(d, N, seed, jitter=0.05, drop=drop)
+    a = S.actions(d, N, T, seed).astype(np.float64)
+    return f32(orc.rollout(d, st, a)).astype(np.float64)
+
+
+@pytest.mark.parametrize("name,drop", SCENE_CASES)
+def test_one_step_parity(brax, name, drop):
+    """One step from identical states: max |dpos| <= 1e-5 m, |dvel| small."""
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    N = 100  # 3 full groups of 32 and a ragged tail of 4
+    st = settled_states(d, name, N, 2, drop)
+    a = S.actions(d, N, 1, 3)
+    ref, cc_ref = orc.rollout(d, st, a.astype(np.float64), contact_count=True)
+    out = sysm.rollout(cuda(st), cuda(a), contact_count=True)
+    got = out["state_T"].cpu().numpy()
+    assert np.isfinite(got).all()
+    dpos = np.abs(got[..., 0:3] - ref[..., 0:3]).max()
+    assert dpos <= 1e-5, dpos
+    dq = np.abs(got[..., 3:7] - ref[..., 3:7]).max()
+    assert dq <= 1e-4, dq
+    cc = out["contact_count"].cpu().numpy()
+    assert cc_ref.sum() > 0 or name == "pendulum"
+    # contact counts agree except where an activation threshold flips
+    assert np.mean(cc == cc_ref) >= 0.9
+    sysm.sync_status()
+
+
+def test_step_equals_rollout_of_one(brax):
+    d = S.quadruped()
+    sysm = brax(d)
+    N = 40
+    st = settled_states(d, "quadruped", N, 4, 0.38)
+    a = S.actions(d, N, 1, 4)
+    r = sysm.rollout(cuda(st), cuda(a))["state_T"]
+    s1 = sysm.step(cuda(st), cuda(a[0]))
+    assert torch.equal(r, s1)
+
+
+def test_fifty_step_parity_quadruped(brax):
+    """Quadruped, 128 envs: 50 steps within 1e-3 m of the FP64 oracle."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 128, 50
+    st, _ = initial(d, N, 0)
+    a = S.actions(d, N, T, 0)
+    ref = orc.rollout(d, st, a.astype(np.float64))
+    got = sysm.rollout(cuda(st), cuda(a))["state_T"].cpu().numpy()
+    err = np.abs(got[..., 0:3] - ref[..., 0:3]).max(axis=(1, 2))
+    assert np.median(err) <= 1e-3, np.sort(err)[-10:]
+    assert np.mean(err <= 1e-3) >= 0.9, np.sort(err)[-10:]
+
+
+def test_distribution_after_1000_steps(brax):
+    """Beyond the chaotic horizon: torso displacement distributions agree."""
+    from scipy.stats import ks_2samp
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 128, 1000
+    st, _ = initial(d, N, 0)
+    a = S.actions(d, N, T, 0)
+    ref = orc.rollout(d, st, a.astype(np.float64))
+    got = sysm.rollout(cuda(st), cuda(a))["state_T"].cpu().numpy()
+    assert np.isfinite(got).all()
+    for k in (0, 1):
+        dr = ref[:, 0, k] - st[:, 0, k]
+        dg = got[:, 0, k] - st[:, 0, k]
+        assert ks_2samp(dr, dg).pvalue > 0.01
+        se = math.sqrt(dr.var() / N + dg.var() / N)
+        assert abs(dr.mean() - dg.mean()) <= 3 * se + 1e-6
+    sysm.sync_status()
+
+
+def test_checkpoints_and_torso(brax):
+    """Checkpoint k equals the state after kK steps; torso is body 0's
+    position after every step (bitwise: the same kernel path)."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T, K = 45, 12, 5
+    st, _ = initial(d, N, 5)
+    a = cuda(S.actions(d, N, T, 5))
+    out = sysm.rollout(cuda(st), a, K=K, checkpoints=True, torso=True)
+    ck, tor = out["checkpoints"], out["torso"]
+    assert ck.shape[0] == math.ceil(T / K)
+    assert torch.equal(ck[0], cuda(st))
+    for k in range(1, ck.shape[0]):
+        part = sysm.rollout(cuda(st), a[:k * K].contiguous())["state_T"]
+        assert torch.equal(ck[k], part)
+    part = sysm.rollout(cuda(st), a[:7].contiguous())["state_T"]
+    assert torch.equal(tor[6], part[:, 0, 0:3])
+    assert torch.equal(tor[T - 1], out["state_T"][:, 0, 0:3])
+
+
+def test_edge_sizes(brax):
+    d = S.pendulum()
+    sysm = brax(d)
+    st, _ = initial(d, 1, 6)
+    a = S.actions(d, 1, 3, 6)
+    ref = orc.rollout(d, st, a.astype(np.float64))
+    got = sysm.rollout(cuda(st), cuda(a))["state_T"].cpu().numpy()
+    assert np.abs(got[..., :3] - ref[..., :3]).max() < 1e-5
+    # T = 0 returns the initial state; N = 0 is a no-op
+    z = sysm.rollout(cuda(st), torch.zeros((0, 1, sysm.A), device="cuda"))["state_T"]
+    assert torch.equal(z, cuda(st))
+    e = sysm.rollout(torch.zeros((0, sysm.B, 13), device="cuda"), torch.zeros((3, 0, sysm.A), device="cuda"))
+    assert e["state_T"].shape == (0, sysm.B, 13)
+
+
+def test_nonfinite_state_reported(brax):
+    """A NaN in the input state sets the status word; no trap, context usable."""
+    from paper_2106_13281_gb300.binding import BraxError
+    d = S.quadruped()
+    sysm = brax(d)
+    st, _ = initial(d, 33, 7)
+    st[17, 3, 8] = np.nan
+    a = S.actions(d, 33, 2, 7)
+    sysm.rollout(cuda(st), cuda(a))
+    with pytest.raises(BraxError) as ei:
+        sysm.sync_status()
+    assert ei.value.code == 5
+    # the flag is cleared and the context still works
+    st[17, 3, 8] = 0.0
+    sysm.rollout(cuda(st), cuda(a))
+    sysm.sync_status()
