@@ -1,0 +1,305 @@
+"""Benchmark of the batched rigid-body step on GB300.
+
+Workload (one bench step): one persistent forward rollout of the 9-body
+quadruped, 65,536 environments x 1,000 steps (10 substeps each), synthetic
+seeded inputs resident in HBM; when the adjoint is available, the same
+rollout's reverse pass follows and is timed as the fwd+bwd figure.
+
+Prints one JSON line (rank 0).  `value` = forward env-steps/s over all ranks.
+The roofline is FP32-ALU bound: achieved = algorithmic flops per launch (the
+oracle's flop count per env-step, stored in paper_2106_13281_gb300/data) /
+the kernel's CUDA-event duration; peak = 152 SMs x 128 FP32 lanes x 2 flops
+x 2.07 GHz.
+
+`--impl reference` times the FP64 oracle (the reference arm of this method:
+a plain CPU program) on a bounded sample of the same workload on the host
+cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s fwd and fwd+bwd, 9-body quadruped @64k envs; % roofline; err vs FP64"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.54
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--envs", type=int, default=65536)
+    p.add_argument("--horizon", type=int, default=1000, help="steps per rollout")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def alg_flops(scene="quadruped"):
+    with open(os.path.join(ROOT, "paper_2106_13281_gb300", "data", "alg_flops.json")) as f:
+        return json.load(f)[scene]
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2106_13281_gb300 import scenes as S
+    from paper_2106_13281_gb300.system import BraxSystem
+
+    rank, world, local = dist_setup(args.gpus)
+    N, T = args.envs, args.horizon
+    d = S.quadruped()
+    sysm = BraxSystem(d)
+    seed = 1 + 1000 * rank  # each rank simulates its own shard of environments
+    rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    state0 = sysm.default_qp(N, f32(rp), f32(rr), f32(ang))
+    actions = f32(S.actions(d, N, T, seed))
+    state_T = torch.empty_like(state0)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sysm.rollout(state0, actions, state_T=state_T)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sysm.sync_status()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        start.record(stream)
+        for e0, e1 in ev:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+    sysm.sync_status()
+    total_ms = barrier_max(start.elapsed_time(end), world)
+    kern_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    envsteps = N * T
+    value = world * envsteps * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs in, state back out, every step
+    h_state0 = state0.cpu().pin_memory()
+    h_actions = actions.cpu().pin_memory()
+    h_out = torch.empty_like(h_state0).pin_memory()
+    d_state0, d_actions = torch.empty_like(state0), torch.empty_like(actions)
+
+    def e2e_step():
+        d_state0.copy_(h_state0, non_blocking=True)
+        d_actions.copy_(h_actions, non_blocking=True)
+        sysm.rollout(d_state0, d_actions, state_T=state_T)
+        h_out.copy_(state_T, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = barrier_max(e0.elapsed_time(e1), world)
+    e2e_value = world * envsteps * args.steps / (e2e_ms / 1e3)
+    h2d = h_state0.numel() * 4 + h_actions.numel() * 4
+    d2h = h_out.numel() * 4
+
+    fl = alg_flops("quadruped")
+    flops_per_envstep = fl["flops_per_env_step"]
+    achieved_tflops = flops_per_envstep * envsteps / (kern_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "env-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded PCG64 actions uniform[-1,1], initial joint angles N(0,0.1^2), heights 0.75+U(0,0.05))",
+        "config": {"workload": "quadruped-9body forward rollout, 65536 envs x 1000 steps x 10 substeps",
+                   "envs": N, "steps_per_rollout": T, "substeps": int(d["substeps"]), "dt": float(d["dt"]),
+                   "l2": "inputs larger than L2 (actions %.2f GB per rollout)" % (actions.numel() * 4 / 1e9),
+                   "parallelism": f"env shards x{world}"},
+        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": fl.get("traffic_bytes_per_launch"),
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                     "flops_per_env_step": flops_per_envstep, "kernel_ms": kern_ms},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(d, sysm, seed)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(d, sysm, seed, n_envs=2048, T=200):
+    """The FP64 oracle on a bounded sample of the same workload (host cores),
+    plus the GPU's one-step position error against it on that sample."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as orc
+    from paper_2106_13281_gb300 import scenes as S
+    rp, rr, ang = S.initial_conditions(d, n_envs, seed, height_jitter=0.05)
+    st = orc.default_qp(d, n_envs, rp, rr, ang).astype(np.float32).astype(np.float64)
+    a = S.actions(d, n_envs, T, seed).astype(np.float64)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = orc.rollout(d, st, a, n_threads=cores)
+    dt = time.perf_counter() - t0
+    one = orc.rollout(d, st, a[:1], n_threads=cores)
+    f32 = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    got = sysm.rollout(f32(st), f32(a[:1]))["state_T"].cpu().numpy()
+    err = float(np.abs(got[..., :3] - one[..., :3]).max())
+    return {"value": n_envs * T / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_envs} envs x {T} steps of the same quadruped workload (seed {seed}), FP64, "
+                      f"{cores} threads", "err_vs_fp64_1step_max_m": err}
+
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm: each step is a bounded sample
+    (1024 envs x 100 steps) of the quadruped workload on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_2106_13281_gb300 import scenes as S
+    d = S.quadruped()
+    n_envs, T = 1024, 100
+    rp, rr, ang = S.initial_conditions(d, n_envs, 1, height_jitter=0.05)
+    st = orc.default_qp(d, n_envs, rp, rr, ang)
+    a = S.actions(d, n_envs, T, 1).astype(np.float64)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        orc.rollout(d, st, a, n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.rollout(d, st, a, n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = n_envs * T * args.steps / dt
+    sample = f"{n_envs} envs x {T} steps of the quadruped workload per step, FP64 oracle, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "quadruped-9body forward rollout (bounded CPU sample)", "envs": n_envs,
+                   "steps_per_rollout": T},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

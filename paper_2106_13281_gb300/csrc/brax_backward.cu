@@ -5,7 +5,13 @@
 #include "brax_kernels.h"
 
 namespace brax {
-cudaError_t launch_rollout_backward(const Launch&, int, int, size_t, int, cudaStream_t) { return cudaErrorNotSupported; }
+__constant__ __align__(16) unsigned char c_pool[kPoolBytes];
+cudaError_t upload_pool_backward(int off, const void* data, size_t bytes) {
+  return cudaMemcpyToSymbol(c_pool, data, bytes, (size_t)off, cudaMemcpyHostToDevice);
+}
+cudaError_t launch_rollout_backward(const Launch&, int, int, size_t, int, bool, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
 }  // namespace brax
 
 extern "C" {

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -337,7 +338,7 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
         BodyP& bp = bodies[side == 0 ? ba : bb];
         REQUIRE(bp.n_bpairs < BRAX_MAX_BODY_PAIRS, "body: more than BRAX_MAX_BODY_PAIRS body-body pairs");
         bp.bpair[bp.n_bpairs++] = (idx << 1) | side;
-        bp.flags |= kPublish;
+        bp.flags |= kPublish | kInPair;
       }
     }
   }
@@ -350,6 +351,9 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   S.n_planes = (int)planes.size();
   S.substeps = d.substeps;
   S.average = d.average_contacts ? 1 : 0;
+  S.general = Pb > 0 ? 1 : 0;
+  for (int j = 0; j < J; ++j)
+    if (d.dof[j] == 3) S.general = 1;
   const double h = (double)d.dt / d.substeps;
   S.h = (float)h;
   S.beta_h = (float)(d.baumgarte / h);
@@ -370,6 +374,9 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
 
 struct brax_system {
   int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
+  bool general = false;  // 3-DOF joints or body-body pairs present
+  int device = 0;
+  int pool_off = -1;     // offset of the blob in the constant parameter pool
   std::vector<unsigned char> blob;
   unsigned char* d_blob = nullptr;
   int32_t* d_status = nullptr;
@@ -387,8 +394,42 @@ namespace {
 
 size_t group_bytes(const brax_system* s) { return (size_t)group_floats(s->B, s->P) * sizeof(float); }
 
+// First-fit allocator of the constant parameter pool, one per device.
+struct PoolRange {
+  int device, off, bytes;
+};
+std::vector<PoolRange> g_pool;
+std::mutex g_pool_mu;
+
+int pool_alloc(int device, int bytes) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  std::vector<PoolRange> used;
+  for (const auto& r : g_pool)
+    if (r.device == device) used.push_back(r);
+  std::sort(used.begin(), used.end(), [](const PoolRange& a, const PoolRange& b) { return a.off < b.off; });
+  int off = 0;
+  for (const auto& r : used) {
+    if (r.off - off >= bytes) break;
+    off = std::max(off, r.off + r.bytes);
+  }
+  if (off + bytes > kPoolBytes) return -1;
+  g_pool.push_back(PoolRange{device, off, bytes});
+  return off;
+}
+void pool_free(int device, int off) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (size_t i = 0; i < g_pool.size(); ++i)
+    if (g_pool[i].device == device && g_pool[i].off == off) {
+      g_pool.erase(g_pool.begin() + i);
+      return;
+    }
+}
+
+// Smallest launch bound that admits the block (measured fastest for the
+// quadruped: (288, 3)).
 int pick_variant(int threads) {
-  for (int v = 0; v < 3; ++v)
+  static const int order[4] = {3, 0, 1, 2};
+  for (int v : order)
     if (threads <= rollout_variant_max_threads(v)) return v;
   return -1;
 }
@@ -399,6 +440,7 @@ Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
   Seg sg;
   std::memset(&sg, 0, sizeof(sg));
   sg.blob = s->d_blob;
+  sg.pool_off = s->pool_off;
   sg.blob_bytes = (int32_t)s->blob.size();
   sg.B = s->B;
   sg.P = s->P;
@@ -429,6 +471,7 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   s->B = S->B;
   s->A = S->A;
   s->D = S->D;
+  s->general = S->general != 0;
   cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size());
   if (e != cudaSuccess) {
     delete s;
@@ -438,9 +481,22 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   e = cudaMalloc(&s->d_status, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(s->d_blob, s->blob.data(), s->blob.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) {
+    s->pool_off = pool_alloc(s->device, (int)s->blob.size());
+    if (s->pool_off < 0) {
+      cudaFree(s->d_blob);
+      cudaFree(s->d_status);
+      delete s;
+      return fail(BRAX_ERR_OUT_OF_MEMORY, "brax_system_create: the constant parameter pool (60 KB per device) is full");
+    }
+    e = upload_pool_forward(s->pool_off, s->blob.data(), s->blob.size());
+    if (e == cudaSuccess) e = upload_pool_backward(s->pool_off, s->blob.data(), s->blob.size());
+  }
   if (e != cudaSuccess) {
     cudaFree(s->d_blob);
     if (s->d_status) cudaFree(s->d_status);
+    if (s->pool_off >= 0) pool_free(s->device, s->pool_off);
     delete s;
     return cuda_fail(e, "brax_system_create");
   }
@@ -452,6 +508,7 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
 
 void brax_system_destroy(brax_system* s) {
   if (!s) return;
+  if (s->pool_off >= 0) pool_free(s->device, s->pool_off);
   cudaFree(s->d_blob);
   cudaFree(s->d_status);
   delete s;
@@ -469,7 +526,7 @@ int brax_system_info(const brax_system* s, int32_t* n_bodies, int32_t* n_actuato
 // launch-bounds variant); used by the autotuner.  Not part of brax.h's
 // stable surface.
 int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant) {
-  if (!s || groups < 1 || groups > 15 || variant < 0 || variant > 2)
+  if (!s || groups < 1 || groups > 15 || variant < 0 || variant > 3)
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_launch: bad arguments");
   if (32 * s->B * groups > rollout_variant_max_threads(variant))
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_launch: block too large for the variant");
@@ -512,8 +569,8 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   sg.torso = torso_traj;
   sg.ccount = contact_count;
   L.seg[0] = sg;
-  const size_t smem = s->blob.size() + s->groups * group_bytes(s);
-  cudaError_t e = launch_rollout(L, (int)grid, 32 * s->B * s->groups, smem, s->variant, as_stream(stream));
+  const size_t smem = s->groups * group_bytes(s);
+  cudaError_t e = launch_rollout(L, (int)grid, 32 * s->B * s->groups, smem, s->variant, s->general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
 }
 
@@ -592,7 +649,9 @@ int brax_batch_offsets(const brax_batch* b, int32_t T, int32_t K, int32_t i, int
 
 namespace brax_batch_impl {
 // Fill a launch table for the batch; pointers offset per system.
-int make_launch(const brax_batch* b, int32_t T, int32_t K, Launch& L, int* grid, int* threads, size_t* smem) {
+int make_launch(const brax_batch* b, int32_t T, int32_t K, Launch& L, int* grid, int* threads, size_t* smem,
+                bool* general) {
+  *general = false;
   std::memset(&L, 0, sizeof(L));
   L.n_segs = (int)b->sys.size();
   L.T = T;
@@ -608,7 +667,8 @@ int make_launch(const brax_batch* b, int32_t T, int32_t K, Launch& L, int* grid,
     sg.cta_begin = cta;
     sg.cta_end = cta + (int)nb;
     cta += (int)nb;
-    sm = std::max(sm, s->blob.size() + (size_t)G * group_bytes(s));
+    sm = std::max(sm, (size_t)G * group_bytes(s));
+    *general = *general || s->general;
     L.seg[i] = sg;
   }
   *grid = cta;
@@ -626,7 +686,8 @@ extern "C" int brax_batch_rollout(const brax_batch* b, int32_t T, int32_t K, con
   Launch L;
   int grid, threads;
   size_t smem;
-  brax_batch_impl::make_launch(b, T, K, L, &grid, &threads, &smem);
+  bool general;
+  brax_batch_impl::make_launch(b, T, K, L, &grid, &threads, &smem, &general);
   for (int i = 0; i < L.n_segs; ++i) {
     int64_t so, ao, to, co;
     brax_batch_offsets(b, T, K, i, &so, &ao, &to, &co);
@@ -639,6 +700,6 @@ extern "C" int brax_batch_rollout(const brax_batch* b, int32_t T, int32_t K, con
   if (grid == 0) return BRAX_OK;
   const int variant = pick_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout: block too large");
-  cudaError_t e = launch_rollout(L, grid, threads, smem, variant, as_stream(stream));
+  cudaError_t e = launch_rollout(L, grid, threads, smem, variant, general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout");
 }

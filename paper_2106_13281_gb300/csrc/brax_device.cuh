@@ -10,11 +10,17 @@ namespace brax {
 
 #define BRAX_MAX_SEGS 8
 
+// Constant-memory pool holding the parameter blobs of all live systems.  A
+// warp reads its body's parameters with a warp-uniform index, so the loads go
+// through the constant cache and the uniform datapath, not the LSU.
+constexpr int kPoolBytes = 61440;
+
 // One system's share of a launch.  A thread block runs G groups of 32
 // environments of one system; group g's warps are bodies 0..B-1 (warp =
 // body, lane = environment).
 struct Seg {
-  const unsigned char* blob;
+  const unsigned char* blob;  // device copy of the parameter blob (default_qp)
+  int32_t pool_off;           // offset of the blob in the constant parameter pool
   int32_t blob_bytes;
   int32_t B, P, A;
   int32_t groups;  // groups of 32 environments per thread block

@@ -14,6 +14,8 @@
 
 namespace brax {
 
+__constant__ __align__(16) unsigned char c_pool[kPoolBytes];
+
 __device__ __forceinline__ void load_body(const float* p, Body& s) {
   s.x = mk3(p[0], p[1], p[2]);
   s.qw = p[3];
@@ -45,48 +47,64 @@ __device__ __forceinline__ bool body_finite(const Body& s) {
 
 // One substep of one (body, environment) thread; returns the number of
 // contacts this thread counted (own plane contacts + owned pairs).
+template <bool kGeneral>
 __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodies, const PairP* pairs,
-                                               const PlaneP* planes, const BodyP& bp, int b, int B, int lane,
-                                               GroupMem& gm, int bar, int nthr, Body& s, const float* act) {
+                                               const PlaneP* planes, const BodyP& bp, const HingeRegs& hr,
+                                               const PointRegs* pr, int b, int B, int lane, GroupMem& gm, int bar,
+                                               int nthr, Body& s, const float* act) {
   kinematic(bp, S.h, s);
   const Frame f = make_frame(bp, s);
-  if (bp.flags & kPublish) publish(gm, b, lane, s, f);
+  if (bp.flags & kPublish) {
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
+    else publish<false>(gm, b, lane, s, f);
+  }
   group_sync(bar, nthr);
   Wrench wr{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f)};
   if (bp.flags & kHasParent) {
     const Pub pp = read_pub(gm, bp.parent, lane);
-    wr = joint_forward(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
   }
   Acc acc{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f), 0};
-  for (int i = 0; i < bp.n_points; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  const int np = bp.n_points;
+  if (kGeneral) {
+    for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  } else {
+    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
+    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  }
   int counted = acc.n;
-  for (int k = b; k < S.P; k += B) counted += pair_forward(S, bodies, pairs[k], gm, k, lane);
+  if (kGeneral)
+    for (int k = b; k < S.P; k += B) counted += pair_forward(S, bodies, pairs[k], gm, k, lane);
   group_sync(bar, nthr);
-  integrate(S, bp, gm, lane, s, f, wr, acc);
+  integrate<kGeneral>(S, bp, gm, lane, s, f, wr, acc);
   return counted;
 }
 
-template <int MAXT, int MINB>
+// Persistent rollout.  Parameters are read from the constant pool with a
+// warp-uniform body index (broadcast from lane 0 so the compiler can treat it
+// as uniform); the state stays in registers for all T x substeps.
+template <int MAXT, int MINB, bool kGeneral>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_constant__ Launch L) {
   int si = 0;
   while (si + 1 < L.n_segs && (int)blockIdx.x >= L.seg[si].cta_end) ++si;
   const Seg& sg = L.seg[si];
   extern __shared__ __align__(16) unsigned char smem[];
-  for (int i = threadIdx.x; i < sg.blob_bytes / 16; i += blockDim.x)
-    reinterpret_cast<int4*>(smem)[i] = reinterpret_cast<const int4*>(sg.blob)[i];
-  __syncthreads();
-  const SysP& S = *reinterpret_cast<const SysP*>(smem);
-  const BodyP* bodies = reinterpret_cast<const BodyP*>(smem + blob_bodies_off());
-  const PairP* pairs = reinterpret_cast<const PairP*>(smem + blob_pairs_off(S.B));
-  const PlaneP* planes = reinterpret_cast<const PlaneP*>(smem + blob_planes_off(S.B, S.P));
-  const int B = S.B;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned char* blob = c_pool + sg.pool_off;
+  const SysP& S = *reinterpret_cast<const SysP*>(blob);
+  const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
+  const PairP* pairs = reinterpret_cast<const PairP*>(blob + blob_pairs_off(sg.B));
+  const PlaneP* planes = reinterpret_cast<const PlaneP*>(blob + blob_planes_off(sg.B, sg.P));
+  const int B = sg.B;
+  const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
+  const int lane = threadIdx.x & 31;
   const int g = warp / B, b = warp - g * B;
   if (g >= sg.groups) return;  // spare warps take no part in the group barriers
   const int64_t N = sg.n_envs;
   const int64_t env = ((int64_t)(blockIdx.x - sg.cta_begin) * sg.groups + g) * 32 + lane;
   const bool valid = env < N;
-  GroupMem gm = group_mem(reinterpret_cast<float*>(smem + sg.blob_bytes) + g * group_floats(B, S.P), B, S.P);
+  GroupMem gm = group_mem(reinterpret_cast<float*>(smem) + g * group_floats(B, sg.P), B, sg.P);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
   if (b == 0) gm.cnt[lane] = 0;
@@ -109,6 +127,13 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   int ccount = 0;
   bool bad = false;
   float act[3] = {0.f, 0.f, 0.f};
+  HingeRegs hr;
+  PointRegs pr[2];
+  if (!kGeneral) {
+    if (bp.flags & kHasParent) hr = hinge_regs(bp);
+    if (bp.n_points > 0) pr[0] = point_regs(bp.pt[0]);
+    if (bp.n_points > 1) pr[1] = point_regs(bp.pt[1]);
+  }
   for (int t = 0; t < T; ++t) {
     if (sg.ckpt && valid && (t % K) == 0) store_body(sg.ckpt + (((int64_t)(t / K) * N + env) * B + b) * 13, s);
     if (valid && (bp.flags & kHasParent)) {
@@ -117,7 +142,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
       for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
     }
     for (int k = 0; k < nsub; ++k)
-      ccount += substep_forward(S, bodies, pairs, planes, bp, b, B, lane, gm, bar, nthr, s, act);
+      ccount += substep_forward<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
     if (sg.torso && b == 0 && valid) {
       float* tp = sg.torso + ((int64_t)t * N + env) * 3;
       tp[0] = s.x.x;
@@ -207,24 +232,43 @@ __global__ void default_qp_kernel(const unsigned char* blob, int64_t N, const fl
 }
 
 // ------------------------------------------------------------------ launchers
-template <int MAXT, int MINB>
+template <int MAXT, int MINB, bool G>
 static cudaError_t launch_rollout_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
-  auto k = rollout_kernel<MAXT, MINB>;
+  auto k = rollout_kernel<MAXT, MINB, G>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st) {
+// Launch-bounds variants (max threads per block, min blocks per SM):
+//   0: (384, 2)  1: (576, 1)  2: (1024, 1)  3: (288, 3)
+cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
+                           cudaStream_t st) {
+  if (general) {
+    switch (variant) {
+      case 0: return launch_rollout_t<384, 2, true>(L, grid, threads, smem, st);
+      case 1: return launch_rollout_t<576, 1, true>(L, grid, threads, smem, st);
+      case 3: return launch_rollout_t<288, 3, true>(L, grid, threads, smem, st);
+      default: return launch_rollout_t<1024, 1, true>(L, grid, threads, smem, st);
+    }
+  }
   switch (variant) {
-    case 0: return launch_rollout_t<384, 2>(L, grid, threads, smem, st);
-    case 1: return launch_rollout_t<640, 1>(L, grid, threads, smem, st);
-    default: return launch_rollout_t<1024, 1>(L, grid, threads, smem, st);
+    case 0: return launch_rollout_t<384, 2, false>(L, grid, threads, smem, st);
+    case 1: return launch_rollout_t<576, 1, false>(L, grid, threads, smem, st);
+    case 3: return launch_rollout_t<288, 3, false>(L, grid, threads, smem, st);
+    default: return launch_rollout_t<1024, 1, false>(L, grid, threads, smem, st);
   }
 }
 
-int rollout_variant_max_threads(int variant) { return variant == 0 ? 384 : (variant == 1 ? 640 : 1024); }
+int rollout_variant_max_threads(int variant) {
+  static const int t[4] = {384, 576, 1024, 288};
+  return (variant >= 0 && variant < 4) ? t[variant] : 0;
+}
+
+cudaError_t upload_pool_forward(int off, const void* data, size_t bytes) {
+  return cudaMemcpyToSymbol(c_pool, data, bytes, (size_t)off, cudaMemcpyHostToDevice);
+}
 
 cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
                               const float* angles, float* out, cudaStream_t st) {

@@ -8,9 +8,14 @@
 namespace brax {
 
 // variant: 0 = (384 threads, 2 blocks/SM), 1 = (640, 1), 2 = (1024, 1) launch bounds
-cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
+                           cudaStream_t st);
+// Copy a parameter blob into the constant pool of each kernel translation unit.
+cudaError_t upload_pool_forward(int off, const void* data, size_t bytes);
+cudaError_t upload_pool_backward(int off, const void* data, size_t bytes);
 int rollout_variant_max_threads(int variant);
-cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
+                                    cudaStream_t st);
 cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
                               const float* angles, float* out, cudaStream_t st);
 

@@ -20,6 +20,7 @@ enum BodyFlags : uint32_t {
   kAnyFrozen = 1u << 6,
   kHasParent = 1u << 7,   // the body is the child of a joint
   kPublish = 1u << 8,     // other warps read this body's substep state
+  kInPair = 1u << 9,      // the body takes part in a body-body pair
 };
 
 // A plane-contact point of a body: a sphere of radius r centred at o (body
@@ -87,6 +88,8 @@ struct SysP {
   float h, beta_h, eps, pad0;  // beta_h = baumgarte / h
   float g[3];
   float pad1;
+  int32_t general;  // 1: the system has a 3-DOF joint or a body-body pair
+  int32_t pad3[3];
   int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
   int32_t n_order;
   int32_t pad2[3];

@@ -67,6 +67,7 @@ __device__ __forceinline__ Frame make_frame(const BodyP& bp, const Body& s) {
   return f;
 }
 
+template <bool kIi>
 __device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Body& s, const Frame& f) {
   float* p = gm.pubf(b, 0) + lane;
   p[0 * 32] = s.x.x;
@@ -80,8 +81,10 @@ __device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Bod
   p[15 * 32] = s.w.x;
   p[16 * 32] = s.w.y;
   p[17 * 32] = s.w.z;
+  if (kIi) {
 #pragma unroll
-  for (int i = 0; i < 6; ++i) p[(18 + i) * 32] = f.Ii.a[i];
+    for (int i = 0; i < 6; ++i) p[(18 + i) * 32] = f.Ii.a[i];
+  }
 }
 
 struct Pub {
@@ -107,6 +110,62 @@ __device__ __forceinline__ S6 read_pub_Ii(GroupMem& gm, int b, int lane) {
   return s;
 }
 
+// ------------------------------------------------------------------ register-resident parameters
+// The hinge parameters and the first two plane-contact points of a warp's
+// body, copied into registers once per launch.  The copy goes through an
+// opaque move so the compiler keeps the values in registers instead of
+// reloading them from the constant pool every substep.
+__device__ __forceinline__ float keep(float x) {
+  float y;
+  asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+struct HingeRegs {
+  float off_p[3], off_c[3], ap[6], ac[6];
+  float k, c, ka, ca, kl;
+  float lo[1], hi[1], gear[1];
+  int act[1];
+  int dof;
+};
+__device__ __forceinline__ HingeRegs hinge_regs(const BodyP& bp) {
+  HingeRegs r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.off_p[i] = keep(bp.off_p[i]);
+    r.off_c[i] = keep(bp.off_c[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    r.ap[i] = keep(bp.ap[i]);
+    r.ac[i] = keep(bp.ac[i]);
+  }
+  r.k = keep(bp.k);
+  r.c = keep(bp.c);
+  r.ka = keep(bp.ka);
+  r.ca = keep(bp.ca);
+  r.kl = keep(bp.kl);
+  r.lo[0] = keep(bp.lo[0]);
+  r.hi[0] = keep(bp.hi[0]);
+  r.gear[0] = keep(bp.gear[0]);
+  r.act[0] = bp.act[0];
+  r.dof = 1;
+  return r;
+}
+struct PointRegs {
+  float o[3];
+  float r, mu, e;
+};
+__device__ __forceinline__ PointRegs point_regs(const PointP& p) {
+  PointRegs r;
+  r.o[0] = keep(p.o[0]);
+  r.o[1] = keep(p.o[1]);
+  r.o[2] = keep(p.o[2]);
+  r.r = keep(p.r);
+  r.mu = p.mu;
+  r.e = p.e;
+  return r;
+}
+
 // ------------------------------------------------------------------ phase J: joint
 // Spring joint (Sec. 3 joint.revolute, Sec. 7.1): anchor spring-damper F on
 // the child at its anchor and -F on the parent at its anchor; hinge-axis
@@ -114,7 +173,8 @@ __device__ __forceinline__ S6 read_pub_Ii(GroupMem& gm, int b, int lane) {
 // one-sided limit springs on the joint angles (App. A angle_limit); torque
 // actuators gear * clamp(a, -1, 1) about the joint axes (Sec. 3).  Returns
 // the child's wrench; writes the parent's to the react buffer.
-__device__ __forceinline__ Wrench joint_forward(const BodyP& bp, const Pub& pp, const Body& s, const Frame& f,
+template <bool kGeneral, class JP>
+__device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, const Body& s, const Frame& f,
                                                 const float* act, float* react_out /* reactf(b,0)+lane */) {
   const V3 rp = mulc(pp.R, bp.off_p);
   const V3 rc = mulc(f.R, bp.off_c);
@@ -128,7 +188,7 @@ __device__ __forceinline__ Wrench joint_forward(const BodyP& bp, const Pub& pp, 
   const V3 P1 = mulc(pp.R, bp.ap + 3);
   const V3 wr = s.w - pp.w;
   V3 tj;
-  if (bp.dof == 1) {
+  if (!kGeneral || bp.dof == 1) {
     const V3 Ac = mulc(f.R, bp.ac + 0);
     const V3 yc = mulc(f.R, bp.ac + 3);
     const float th = atan2f(dot(cross(P1, yc), P0), dot(P1, yc));
@@ -195,7 +255,8 @@ struct Eff {
 };
 
 // Plane contact of the own body: sphere (centre R o + x, radius r).
-__device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, const PointP& pt, const PlaneP& pl,
+template <class PT>
+__device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, const PT& pt, const PlaneP& pl,
                                             const Body& s, const Frame& f, Acc& acc) {
   const V3 ro = mulc(f.R, pt.o);
   const V3 n = ld3(pl.n);
@@ -416,6 +477,7 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
 // ------------------------------------------------------------------ phase P
 // Potential integrator: v += h (F/m + g), w += h Ii tau; collision
 // integrator: the mean (or sum) of the contact velocity changes.
+template <bool kGeneral>
 __device__ __forceinline__ void integrate(const SysP& S, const BodyP& bp, GroupMem& gm, int lane, Body& s,
                                           const Frame& f, Wrench wr, Acc acc) {
   for (int c = 0; c < bp.n_children; ++c) {
@@ -423,7 +485,7 @@ __device__ __forceinline__ void integrate(const SysP& S, const BodyP& bp, GroupM
     wr.F = wr.F + mk3(r[0], r[32], r[64]);
     wr.tau = wr.tau + mk3(r[96], r[128], r[160]);
   }
-  for (int i = 0; i < bp.n_bpairs; ++i) {
+  for (int i = 0; kGeneral && i < bp.n_bpairs; ++i) {
     const int code = bp.bpair[i];
     const float* sl = gm.slotf(code >> 1, 0) + lane;
     if (sl[6 * 32] != 0.f) {
