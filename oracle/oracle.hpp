@@ -194,7 +194,16 @@ template <class T> struct Frame {
 
 struct Diag {
   int64_t active_contacts = 0;
+  uint64_t branch_hash = 1469598103934665603ull;  // FNV-1a over every branch decision taken
+  void branch(int code) {
+    branch_hash ^= (uint64_t)(code + 1);
+    branch_hash *= 1099511628211ull;
+  }
 };
+inline thread_local Diag* tl_diag = nullptr;
+inline void note_branch(int code) {
+  if (tl_diag) tl_diag->branch(code);
+}
 
 inline void set_cat(int c) {
   if (tl_flops) tl_flops->cat = c;
@@ -307,6 +316,7 @@ template <class T> inline void joint_apply(const System& s, int j, const Body<T>
     T L(0.0);
     if (val(th) < lo) L = T(s.kl[j]) * (T(lo) - th);
     else if (val(th) > hi) L = T(s.kl[j]) * (T(hi) - th);
+    note_branch(val(th) < lo ? 1 : (val(th) > hi ? 2 : 3));
     V3<T> tl = L * P[a];
     tc = tc + tl;
     tp = tp - tl;
@@ -327,6 +337,7 @@ template <class T> inline void actuator_apply(const System& s, int k, const T* a
   const int p = s.parent[j], c = s.child[j];
   V3<T> ax = mulc(fr[p].R, s.ap(j, s.act_axis[k]));
   T a = vclamp(act[k], -1.0, 1.0);
+  note_branch(40 + (val(act[k]) >= 1.0 ? 1 : (val(act[k]) <= -1.0 ? 2 : 0)));
   V3<T> tau = (T(s.gear[k]) * a) * ax;
   dp[c].tau = dp[c].tau + tau;
   dp[p].tau = dp[p].tau - tau;
@@ -595,6 +606,7 @@ template <class T> inline void respond(const System& s, const Contact<T>& ct, co
   T un = dot(u, ct.n);
   T target = vmax(T(s.baumgarte / h) * ct.depth, T(-ct.e) * un);
   T jn = vmax((target - un) / kn, T(0.0));
+  note_branch(10 + (val(jn) > 0.0 ? 1 : 0) + (val(target) == val(T(-ct.e) * un) ? 2 : 0));
   V3<T> J = jn * ct.n;
   V3<T> ut = u - un * ct.n;
   T ut2 = dot(ut, ut);
@@ -604,7 +616,10 @@ template <class T> inline void respond(const System& s, const Contact<T>& ct, co
     T kt = eff_mass_term(s, a, fr[a], la, tt);
     if (b >= 0) kt = kt + eff_mass_term(s, b, fr[b], lb, tt);
     T jt = vmin(utn / kt, T(ct.mu) * jn);
+    note_branch(val(utn / kt) < val(T(ct.mu) * jn) ? 20 : 21);
     J = J - jt * tt;
+  } else {
+    note_branch(22);
   }
   acc[a].dv = acc[a].dv + mask(s, &s.fpos[3 * a], T(1.0 / s.mass[a]) * J);
   acc[a].dw = acc[a].dw + mask(s, &s.frot[3 * a], mul(fr[a].Ii, cross(la, J)));
@@ -615,6 +630,7 @@ template <class T> inline void respond(const System& s, const Contact<T>& ct, co
     acc[b].n += 1;
   }
   if (dg) dg->active_contacts += 1;
+  note_branch(30 + ct.a * 64 + (ct.b + 1));
 }
 
 // ============================================================ one substep (Algorithm 1)

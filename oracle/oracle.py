@@ -116,7 +116,7 @@ def lib():
             L = C.CDLL(_LIB)
             P = C.c_void_p
             i64, i32 = C.c_int64, C.c_int32
-            L.orc_rollout.argtypes = [P, i64, i32, P, P, P, P, P, i32]
+            L.orc_rollout.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
             L.orc_flops.argtypes = [P, i64, i32, P, P, P, P]
             L.orc_vjp.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
             L.orc_jvp.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
@@ -149,9 +149,11 @@ def _threads(n_threads):
     return n_threads if n_threads else (os.cpu_count() or 1)
 
 
-def rollout(system, state0, actions, traj=False, n_threads=0, contact_count=False):
+def rollout(system, state0, actions, traj=False, n_threads=0, contact_count=False, branch_signature=False):
     """FP64 rollout.  state0 [N,B,13], actions [T,N,A] -> state_T [N,B,13]
-    (+ traj [T,N,B,13] of states after every step, + active contacts [N])."""
+    (+ traj [T,N,B,13] of states after every step, + active contacts [N],
+    + a hash of every branch decision taken [N] (contact activation,
+    friction stick/slip, limits, action clamps))."""
     s = _sys(system)
     state0 = _f64(state0)
     actions = _f64(actions)
@@ -159,12 +161,16 @@ def rollout(system, state0, actions, traj=False, n_threads=0, contact_count=Fals
     out = np.empty_like(state0)
     tr = np.empty((T, N, s.B, 13)) if traj else None
     cc = np.zeros(N, dtype=np.int64) if contact_count else None
-    lib().orc_rollout(C.byref(s.c), N, T, _p(state0), _p(actions), _p(out), _p(tr), _p(cc), _threads(n_threads))
+    sig = np.zeros(N, dtype=np.uint64) if branch_signature else None
+    lib().orc_rollout(C.byref(s.c), N, T, _p(state0), _p(actions), _p(out), _p(tr), _p(cc), _p(sig),
+                      _threads(n_threads))
     res = [out]
     if traj:
         res.append(tr)
     if contact_count:
         res.append(cc)
+    if branch_signature:
+        res.append(sig)
     return res[0] if len(res) == 1 else tuple(res)
 
 

@@ -147,21 +147,24 @@ extern "C" {
 // [T, N, B, 13].  contact_count (optional): active contacts summed over all
 // substeps, per environment.
 int orc_rollout(const orc_desc* d, int64_t N, int32_t T, const double* state0, const double* actions,
-                double* state_T, double* traj, int64_t* contact_count, int32_t n_threads) {
+                double* state_T, double* traj, int64_t* contact_count, uint64_t* branch_sig, int32_t n_threads) {
   System s = make_system(d);
   const int B = s.B, A = s.A;
   parallel_for(N, n_threads, [&](int64_t n) {
     std::vector<Body<double>> qp;
     load_env(s, state0 + n * B * 13, qp);
     Diag dg;
+    tl_diag = &dg;
     std::vector<double> act(A > 0 ? A : 1);
     for (int t = 0; t < T; ++t) {
       for (int a = 0; a < A; ++a) act[a] = actions[((int64_t)t * N + n) * A + a];
       step(s, qp.data(), act.data(), &dg);
       if (traj) store_env(s, qp, traj + ((int64_t)t * N + n) * B * 13);
     }
+    tl_diag = nullptr;
     store_env(s, qp, state_T + n * B * 13);
     if (contact_count) contact_count[n] = dg.active_contacts;
+    if (branch_sig) branch_sig[n] = dg.branch_hash;
   });
   return 0;
 }

@@ -1,34 +1,398 @@
-// Reverse-mode kernels (filled in by the adjoint implementation).
+// Reverse-mode rollout kernel and its C ABI (brax_workspace_size,
+// brax_rollout_backward, the batch variants).
+//
+// Memory plan per group of 32 environments (workspace, caller-owned):
+//   steps  [K][13][B][32]  states at the start of every step of one
+//                          checkpoint segment (recomputed from the segment's
+//                          checkpoint);
+//   subs   [S][13][B][32]  states at the start of every substep of one step
+//                          (recomputed from that step's state);
+//   slots  [P][8][32]      body-body pair impulses of the current substep
+//                          (systems with pairs only).
+// The reverse of a substep recomputes its forward intermediates (two group
+// barriers, as in the forward), then runs the adjoint in reverse order:
+//   P  potential + collision integrators          -> gwr[b] (dL/dF, dL/dtau)
+//   -- barrier --
+//   J  joint (child side; parent adjoints -> gpub[b]), own plane contacts,
+//      owned pairs (adjoints added to gpair[] of both bodies)
+//   -- barrier --
+//   K  gather children's gpub and gpair, frame and kinematic integrator.
+// Every thread of a group holds one (body, environment) and its 13-float
+// adjoint in registers for the whole reverse sweep.
 #include <cuda_runtime.h>
 
+#include <cstring>
+#include <string>
+
 #include "../../include/brax.h"
+#include "brax_adjoint.cuh"
 #include "brax_kernels.h"
 
 namespace brax {
+
 __constant__ __align__(16) unsigned char c_pool[kPoolBytes];
+
+// Backward shared memory of one group (floats), after the forward layout.
+__host__ __device__ inline int bwd_extra_floats(int B, int P) {
+  return B * 6 * 32 + B * 18 * 32 + (P > 0 ? B * 6 * 32 + B * 18 * 32 : 0);
+}
+__host__ __device__ inline int bwd_fwd_floats(int B, int P, bool slots_in_smem) {
+  return B * kPubFields * 32 + B * 6 * 32 + (slots_in_smem ? P * 8 * 32 : 0) + 32;
+}
+__host__ __device__ inline int bwd_group_floats(int B, int P) { return bwd_fwd_floats(B, P, false) + bwd_extra_floats(B, P); }
+__host__ __device__ inline int64_t ws_group_floats(int B, int P, int K, int S) {
+  return (int64_t)(K + S) * 13 * B * 32 + (int64_t)P * 8 * 32;
+}
+
+struct BwdMem {
+  float* gwr;    // [B][6][32]  adjoint of a body's summed force, torque
+  float* gpub;   // [B][18][32] a child's adjoints of its parent's x1, R, v, w
+  float* gacc;   // [B][6][32]  adjoint of a body's contact velocity update (pairs)
+  float* gpair;  // [B][18][32] pair adjoints of a body's x1, R, v, w (atomics)
+};
+
+__device__ __forceinline__ void load_body_ws(const float* p, int stride, Body& s) {
+  s.x = mk3(p[0], p[stride], p[2 * stride]);
+  s.qw = p[3 * stride];
+  s.qx = p[4 * stride];
+  s.qy = p[5 * stride];
+  s.qz = p[6 * stride];
+  s.v = mk3(p[7 * stride], p[8 * stride], p[9 * stride]);
+  s.w = mk3(p[10 * stride], p[11 * stride], p[12 * stride]);
+}
+__device__ __forceinline__ void store_body_ws(float* p, int stride, const Body& s) {
+  p[0] = s.x.x;
+  p[stride] = s.x.y;
+  p[2 * stride] = s.x.z;
+  p[3 * stride] = s.qw;
+  p[4 * stride] = s.qx;
+  p[5 * stride] = s.qy;
+  p[6 * stride] = s.qz;
+  p[7 * stride] = s.v.x;
+  p[8 * stride] = s.v.y;
+  p[9 * stride] = s.v.z;
+  p[10 * stride] = s.w.x;
+  p[11 * stride] = s.w.y;
+  p[12 * stride] = s.w.z;
+}
+
+template <bool kGeneral>
+__device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, const PairP* pairs,
+                                            const PlaneP* planes, const BodyP& bp, const HingeRegs& hr,
+                                            const PointRegs* pr, int b, int B, int lane, GroupMem& gm, int bar,
+                                            int nthr, Body& s, const float* act) {
+  kinematic(bp, S.h, s);
+  const Frame f = make_frame(bp, s);
+  if (bp.flags & kPublish) {
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
+    else publish<false>(gm, b, lane, s, f);
+  }
+  group_sync(bar, nthr);
+  Wrench wr{zero3(), zero3()};
+  if (bp.flags & kHasParent) {
+    const Pub pp = read_pub(gm, bp.parent, lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+  }
+  Acc acc{zero3(), zero3(), 0};
+  const int np = bp.n_points;
+  if (kGeneral) {
+    for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+    for (int k = b; k < S.P; k += B) pair_forward(S, bodies, pairs[k], gm, k, lane);
+  } else {
+    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
+    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  }
+  group_sync(bar, nthr);
+  integrate<kGeneral>(S, bp, gm, lane, s, f, wr, acc);
+}
+
+// Reverse of one substep.  s_in: the substep's input state; g: adjoint of
+// its output state (updated in place to the adjoint of the input state).
+template <bool kGeneral>
+__device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, const PairP* pairs,
+                                            const PlaneP* planes, const BodyP& bp, const HingeRegs& hr,
+                                            const PointRegs* pr, int b, int B, int lane, GroupMem& gm, BwdMem& bm,
+                                            int bar, int nthr, const Body& s_in, GBody& g, const float* act,
+                                            float* gact) {
+  const float h = S.h;
+  // ---- forward recompute: phase K
+  Body s = s_in;
+  kinematic(bp, h, s);
+  const Frame f = make_frame(bp, s);
+  if (bp.flags & kPublish) {
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
+    else publish<false>(gm, b, lane, s, f);
+  }
+  group_sync(bar, nthr);
+  // ---- forward recompute: phase J
+  Wrench wr{zero3(), zero3()};
+  Pub pp;
+  if (bp.flags & kHasParent) {
+    pp = read_pub(gm, bp.parent, lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+  }
+  Acc acc{zero3(), zero3(), 0};
+  const int np = bp.n_points;
+  if (kGeneral) {
+    for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  } else {
+    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
+    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+  }
+  group_sync(bar, nthr);
+  // ---- forward values of phase P
+  V3 Ft = wr.F, Tt = wr.tau;
+  for (int c = 0; c < bp.n_children; ++c) {
+    const float* r = gm.reactf(bp.children[c], 0) + lane;
+    Ft = Ft + mk3(r[0], r[32], r[64]);
+    Tt = Tt + mk3(r[96], r[128], r[160]);
+  }
+  // ---- reverse P: potential and collision integrators
+  const int n = acc.n;
+  const float inv = n > 0 ? ((S.average && n > 1) ? __fdividef(1.f, (float)n) : 1.f) : 0.f;
+  const V3 gdv = inv * g.v, gdw = inv * g.w;
+  V3 gv2 = g.v, gw2 = g.w;
+  if (bp.flags & kAnyFrozen) {
+    gv2 = mask3(bp.flags, gv2);
+    gw2 = mask3(bp.flags >> 3, gw2);
+  }
+  V3 gvm = gv2, gwm = gw2;
+  const V3 gFt = (h * bp.inv_mass) * gv2;
+  S6 gI;
+  zero(gI);
+  V3 gTt = zero3();
+  s6_mul_bwd(f.Ii, Tt, h * gw2, gI, gTt);
+  {
+    float* o = bm.gwr + (b * 6) * 32 + lane;
+    o[0] = gFt.x;
+    o[32] = gFt.y;
+    o[64] = gFt.z;
+    o[96] = gTt.x;
+    o[128] = gTt.y;
+    o[160] = gTt.z;
+  }
+  group_sync(bar, nthr);
+  // ---- reverse J
+  V3 gx1 = g.x;
+  M3 gR;
+  zero(gR);
+  if (bp.flags & kHasParent) {
+    const float* pg = bm.gwr + (bp.parent * 6) * 32 + lane;
+    const V3 gFp = mk3(pg[0], pg[32], pg[64]);
+    const V3 gTp = mk3(pg[96], pg[128], pg[160]);
+    V3 gxp = zero3(), gvp = zero3(), gwp = zero3();
+    M3 gRp;
+    zero(gRp);
+    if (kGeneral) joint_hinge_bwd(bp, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    else joint_hinge_bwd(hr, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    float* o = bm.gpub + (b * 18) * 32 + lane;
+    o[0] = gxp.x;
+    o[32] = gxp.y;
+    o[64] = gxp.z;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[(3 + i) * 32] = gRp.m[i];
+    o[12 * 32] = gvp.x;
+    o[13 * 32] = gvp.y;
+    o[14 * 32] = gvp.z;
+    o[15 * 32] = gwp.x;
+    o[16 * 32] = gwp.y;
+    o[17 * 32] = gwp.z;
+  }
+  if (n > 0) {
+    if (kGeneral) {
+      for (int i = 0; i < np; ++i)
+        plane_point_bwd(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+    } else {
+      if (np > 0) plane_point_bwd(S, bp, pr[0], planes[bp.pt[0].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+      if (np > 1) plane_point_bwd(S, bp, pr[1], planes[bp.pt[1].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+      for (int i = 2; i < np; ++i)
+        plane_point_bwd(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+    }
+  }
+  group_sync(bar, nthr);
+  // ---- reverse K: gather children's adjoints of this body, frame, kinematic
+  for (int c = 0; c < bp.n_children; ++c) {
+    const float* o = bm.gpub + (bp.children[c] * 18) * 32 + lane;
+    gx1 = gx1 + mk3(o[0], o[32], o[64]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gR.m[i] += o[(3 + i) * 32];
+    gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
+    gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
+  }
+  inv_inertia_bwd(f.R, bp.inv_I, gI, gR);
+  float gq1[4] = {g.q[0], g.q[1], g.q[2], g.q[3]};
+  qmat_bwd(s.qw, s.qx, s.qy, s.qz, gR, gq1);
+  g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);
+}
+
+template <int MAXT, int MINB, bool kGeneral>
+__global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_constant__ Launch L) {
+  int si = 0;
+  while (si + 1 < L.n_segs && (int)blockIdx.x >= L.seg[si].cta_end) ++si;
+  const Seg& sg = L.seg[si];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned char* blob = c_pool + sg.pool_off;
+  const SysP& S = *reinterpret_cast<const SysP*>(blob);
+  const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
+  const PairP* pairs = reinterpret_cast<const PairP*>(blob + blob_pairs_off(sg.B));
+  const PlaneP* planes = reinterpret_cast<const PlaneP*>(blob + blob_planes_off(sg.B, sg.P));
+  const int B = sg.B, P = sg.P;
+  const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
+  const int lane = threadIdx.x & 31;
+  const int g = warp / B, b = warp - g * B;
+  if (g >= sg.groups) return;
+  const int64_t N = sg.n_envs;
+  const int64_t group = (int64_t)(blockIdx.x - sg.cta_begin) * sg.groups + g;
+  const int64_t env = group * 32 + lane;
+  const bool valid = env < N;
+  float* gbase = reinterpret_cast<float*>(smem) + g * bwd_group_floats(B, P);
+  GroupMem gm = group_mem(gbase, B, 0);
+  const int K = L.K, T = L.T, nsub = S.substeps;
+  float* ws = sg.ws + group * ws_group_floats(B, P, K, nsub);
+  if (kGeneral) gm.slot = ws + (int64_t)(K + nsub) * 13 * B * 32;  // pair impulses live in the workspace
+  BwdMem bm;
+  bm.gwr = gbase + bwd_fwd_floats(B, P, false);
+  bm.gpub = bm.gwr + B * 6 * 32;
+  bm.gacc = bm.gpub + B * 18 * 32;
+  bm.gpair = bm.gacc + B * 6 * 32;
+  const int bar = 1 + g, nthr = 32 * B;
+  const BodyP& bp = bodies[b];
+  const int stride = B * 32;
+  float* ws_steps = ws + b * 32 + lane;
+  float* ws_subs = ws + (int64_t)K * 13 * B * 32 + b * 32 + lane;
+
+  HingeRegs hr;
+  PointRegs pr[2];
+  if (!kGeneral) {
+    if (bp.flags & kHasParent) hr = hinge_regs(bp);
+    if (bp.n_points > 0) pr[0] = point_regs(bp.pt[0]);
+    if (bp.n_points > 1) pr[1] = point_regs(bp.pt[1]);
+  }
+  GBody gs = zero_gbody();
+  if (valid) {
+    const float* p = sg.g_state_T + (env * B + b) * 13;
+    gs.x = mk3(p[0], p[1], p[2]);
+    gs.q[0] = p[3];
+    gs.q[1] = p[4];
+    gs.q[2] = p[5];
+    gs.q[3] = p[6];
+    gs.v = mk3(p[7], p[8], p[9]);
+    gs.w = mk3(p[10], p[11], p[12]);
+  }
+  const int A = sg.A;
+  const int nseg = (T + K - 1) / K;
+  float act[3] = {0.f, 0.f, 0.f};
+  auto load_act = [&](int t) {
+    if (valid && (bp.flags & kHasParent)) {
+      const float* ap = sg.actions + ((int64_t)t * N + env) * A;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
+    }
+  };
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int t0 = seg * K, t1 = min(T, t0 + K);
+    Body s;
+    if (valid) {
+      load_body(sg.ckpt + (((int64_t)seg * N + env) * B + b) * 13, s);
+    } else {
+      s.x = ld3(bp.rest_pos);
+      s.qw = bp.rest_rot[0];
+      s.qx = bp.rest_rot[1];
+      s.qy = bp.rest_rot[2];
+      s.qz = bp.rest_rot[3];
+      s.v = zero3();
+      s.w = zero3();
+    }
+    // recompute the segment's step states
+    for (int t = t0; t < t1; ++t) {
+      store_body_ws(ws_steps + (int64_t)(t - t0) * 13 * stride, stride, s);
+      if (t + 1 < t1) {
+        load_act(t);
+        for (int k = 0; k < nsub; ++k)
+          fwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
+      }
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      load_body_ws(ws_steps + (int64_t)(t - t0) * 13 * stride, stride, s);
+      load_act(t);
+      for (int k = 0; k < nsub; ++k) {
+        store_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, s);
+        if (k + 1 < nsub)
+          fwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
+      }
+      if (sg.g_torso && b == 0 && valid) {
+        const float* gt = sg.g_torso + ((int64_t)t * N + env) * 3;
+        gs.x = gs.x + mk3(gt[0], gt[1], gt[2]);
+      }
+      float gact[3] = {0.f, 0.f, 0.f};
+      for (int k = nsub - 1; k >= 0; --k) {
+        Body sin;
+        load_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, sin);
+        bwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bm, bar, nthr, sin, gs, act,
+                              gact);
+      }
+      if (valid && sg.g_actions && (bp.flags & kHasParent)) {
+        float* ga = sg.g_actions + ((int64_t)t * N + env) * A;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (bp.act[a] >= 0) ga[bp.act[a]] = gact[a];
+      }
+    }
+  }
+  if (valid && sg.g_state0) {
+    float* p = sg.g_state0 + (env * B + b) * 13;
+    p[0] = gs.x.x;
+    p[1] = gs.x.y;
+    p[2] = gs.x.z;
+    p[3] = gs.q[0];
+    p[4] = gs.q[1];
+    p[5] = gs.q[2];
+    p[6] = gs.q[3];
+    p[7] = gs.v.x;
+    p[8] = gs.v.y;
+    p[9] = gs.v.z;
+    p[10] = gs.w.x;
+    p[11] = gs.w.y;
+    p[12] = gs.w.z;
+  }
+}
+
+template <int MAXT, int MINB, bool G>
+static cudaError_t launch_bwd_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
+  auto k = rollout_bwd_kernel<MAXT, MINB, G>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
+                                    cudaStream_t st) {
+  if (general) {
+    switch (variant) {
+      case 0: return launch_bwd_t<384, 2, true>(L, grid, threads, smem, st);
+      case 1: return launch_bwd_t<576, 1, true>(L, grid, threads, smem, st);
+      case 3: return launch_bwd_t<288, 3, true>(L, grid, threads, smem, st);
+      default: return launch_bwd_t<1024, 1, true>(L, grid, threads, smem, st);
+    }
+  }
+  switch (variant) {
+    case 0: return launch_bwd_t<384, 2, false>(L, grid, threads, smem, st);
+    case 1: return launch_bwd_t<576, 1, false>(L, grid, threads, smem, st);
+    case 3: return launch_bwd_t<288, 3, false>(L, grid, threads, smem, st);
+    default: return launch_bwd_t<1024, 1, false>(L, grid, threads, smem, st);
+  }
+}
+
 cudaError_t upload_pool_backward(int off, const void* data, size_t bytes) {
   return cudaMemcpyToSymbol(c_pool, data, bytes, (size_t)off, cudaMemcpyHostToDevice);
 }
-cudaError_t launch_rollout_backward(const Launch&, int, int, size_t, int, bool, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-}  // namespace brax
 
-extern "C" {
-int brax_workspace_size(const brax_system*, int64_t, int32_t, int32_t, size_t* bytes) {
-  if (bytes) *bytes = 0;
-  return BRAX_ERR_INVALID_ARGUMENT;
-}
-int brax_rollout_backward(const brax_system*, int64_t, int32_t, int32_t, const float*, const float*, const float*,
-                          const float*, const float*, float*, float*, void*, size_t, void*) {
-  return BRAX_ERR_INVALID_ARGUMENT;
-}
-int brax_batch_workspace_size(const brax_batch*, int32_t, int32_t, size_t* bytes) {
-  if (bytes) *bytes = 0;
-  return BRAX_ERR_INVALID_ARGUMENT;
-}
-int brax_batch_rollout_backward(const brax_batch*, int32_t, int32_t, const float*, const float*, const float*,
-                                const float*, const float*, float*, float*, void*, size_t, void*) {
-  return BRAX_ERR_INVALID_ARGUMENT;
-}
-}
+size_t backward_smem_bytes(int B, int P, int groups) { return (size_t)groups * bwd_group_floats(B, P) * sizeof(float); }
+int64_t backward_ws_floats_per_group(int B, int P, int K, int S) { return ws_group_floats(B, P, K, S); }
+
+}  // namespace brax

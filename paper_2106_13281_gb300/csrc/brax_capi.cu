@@ -703,3 +703,128 @@ extern "C" int brax_batch_rollout(const brax_batch* b, int32_t T, int32_t K, con
   cudaError_t e = launch_rollout(L, grid, threads, smem, variant, general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout");
 }
+
+// ------------------------------------------------------------------ reverse mode
+namespace {
+
+// One group of 32 environments per block for the reverse kernel.
+int64_t bwd_groups_total(int64_t n_envs) { return (n_envs + 31) / 32; }
+
+int check_bwd_system(const brax_system* s) {
+  if (s->general) {
+    const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
+    if (S->P > 0)
+      return fail(BRAX_ERR_INVALID_ARGUMENT,
+                  "reverse mode: systems with body-body collision pairs are not supported by this build");
+    for (int b = 0; b < s->B; ++b) {
+      const BodyP* bp = reinterpret_cast<const BodyP*>(s->blob.data() + blob_bodies_off()) + b;
+      if (bp->dof == 3)
+        return fail(BRAX_ERR_INVALID_ARGUMENT, "reverse mode: 3-DOF joints are not supported by this build");
+    }
+  }
+  return BRAX_OK;
+}
+
+size_t bwd_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
+  const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
+  return (size_t)bwd_groups_total(n_envs) * (size_t)backward_ws_floats_per_group(s->B, s->P, K, S->substeps) *
+         sizeof(float);
+}
+
+}  // namespace
+
+extern "C" int brax_workspace_size(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, size_t* bytes) {
+  if (!s || !bytes || n_envs < 0 || T < 0 || K < 1)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_workspace_size: bad arguments");
+  *bytes = bwd_ws_bytes(s, n_envs, std::min(K, std::max(T, 1)));
+  return BRAX_OK;
+}
+
+extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                                     const float* actions, const float* checkpoints, const float* g_state_T,
+                                     const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  if (!s || n_envs < 0 || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: bad arguments");
+  int rc = check_bwd_system(s);
+  if (rc != BRAX_OK) return rc;
+  if (n_envs == 0) return BRAX_OK;
+  if (!g_state_T) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: g_state_T is required");
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (g_state0) {
+      cudaError_t e = cudaMemcpyAsync(g_state0, g_state_T, (size_t)n_envs * s->B * 13 * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "brax_rollout_backward");
+    }
+    return BRAX_OK;
+  }
+  if (!state0 || !checkpoints || (s->A > 0 && !actions))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: state0, actions and checkpoints are required");
+  const int32_t Ke = std::min(K, T);
+  const size_t need = bwd_ws_bytes(s, n_envs, Ke);
+  if (!workspace || workspace_bytes < need)
+    return fail(BRAX_ERR_WORKSPACE, "brax_rollout_backward: workspace missing or smaller than brax_workspace_size");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(BRAX_ERR_WORKSPACE, "brax_rollout_backward: workspace must be 256-byte aligned");
+  Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_segs = 1;
+  L.T = T;
+  L.K = K;  // segment boundaries follow the checkpoints written with K
+  Seg sg = make_seg(s, 1, n_envs);
+  const int64_t grid = bwd_groups_total(n_envs);
+  if (grid > 0x7fffffff) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: too many environments");
+  sg.cta_begin = 0;
+  sg.cta_end = (int32_t)grid;
+  sg.state0 = state0;
+  sg.actions = actions;
+  sg.ckpt = const_cast<float*>(checkpoints);
+  sg.g_state_T = g_state_T;
+  sg.g_torso = g_torso_traj;
+  sg.g_actions = g_actions;
+  sg.g_state0 = g_state0;
+  sg.ws = reinterpret_cast<float*>(workspace);
+  L.seg[0] = sg;
+  const int threads = 32 * s->B;
+  const int variant = pick_variant(threads);
+  if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: system too large for one block");
+  const size_t smem = backward_smem_bytes(s->B, s->P, 1);
+  cudaError_t e = launch_rollout_backward(L, (int)grid, threads, smem, variant, s->general, st);
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_backward");
+}
+
+extern "C" int brax_batch_workspace_size(const brax_batch* b, int32_t T, int32_t K, size_t* bytes) {
+  if (!b || !bytes || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_workspace_size: bad arguments");
+  size_t tot = 0;
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    tot += (bwd_ws_bytes(b->sys[i], b->n_envs[i], std::min(K, std::max(T, 1))) + 255) & ~size_t(255);
+  *bytes = tot;
+  return BRAX_OK;
+}
+
+extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32_t K, const float* state0,
+                                           const float* actions, const float* checkpoints, const float* g_state_T,
+                                           const float* g_torso_traj, float* g_actions, float* g_state0,
+                                           void* workspace, size_t workspace_bytes, void* stream) {
+  if (!b || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: bad arguments");
+  size_t need = 0;
+  brax_batch_workspace_size(b, T, K, &need);
+  if (T > 0 && (!workspace || workspace_bytes < need))
+    return fail(BRAX_ERR_WORKSPACE, "brax_batch_rollout_backward: workspace missing or too small");
+  // one launch per system of the batch, all on the same stream
+  size_t ws_off = 0;
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    int64_t so, ao, to, co;
+    brax_batch_offsets(b, T, K, (int32_t)i, &so, &ao, &to, &co);
+    const brax_system* s = b->sys[i];
+    const size_t wb = bwd_ws_bytes(s, b->n_envs[i], std::min(K, std::max(T, 1)));
+    int rc = brax_rollout_backward(s, b->n_envs[i], T, K, state0 + so, actions ? actions + ao : nullptr,
+                                   checkpoints ? checkpoints + co : nullptr, g_state_T + so,
+                                   g_torso_traj ? g_torso_traj + to : nullptr, g_actions ? g_actions + ao : nullptr,
+                                   g_state0 ? g_state0 + so : nullptr,
+                                   workspace ? reinterpret_cast<char*>(workspace) + ws_off : nullptr, wb, stream);
+    if (rc != BRAX_OK) return rc;
+    ws_off += (wb + 255) & ~size_t(255);
+  }
+  return BRAX_OK;
+}

@@ -16,6 +16,8 @@ cudaError_t upload_pool_backward(int off, const void* data, size_t bytes);
 int rollout_variant_max_threads(int variant);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);
+size_t backward_smem_bytes(int B, int P, int groups);
+int64_t backward_ws_floats_per_group(int B, int P, int K, int S);
 cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
                               const float* angles, float* out, cudaStream_t st);
 

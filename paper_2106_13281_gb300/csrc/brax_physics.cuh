@@ -38,6 +38,36 @@ struct Acc {
   int n;
 };
 
+// ------------------------------------------------------------------ state I/O (QP layout, 13 floats)
+__device__ __forceinline__ void load_body(const float* p, Body& s) {
+  s.x = mk3(p[0], p[1], p[2]);
+  s.qw = p[3];
+  s.qx = p[4];
+  s.qy = p[5];
+  s.qz = p[6];
+  s.v = mk3(p[7], p[8], p[9]);
+  s.w = mk3(p[10], p[11], p[12]);
+}
+__device__ __forceinline__ void store_body(float* p, const Body& s) {
+  p[0] = s.x.x;
+  p[1] = s.x.y;
+  p[2] = s.x.z;
+  p[3] = s.qw;
+  p[4] = s.qx;
+  p[5] = s.qy;
+  p[6] = s.qz;
+  p[7] = s.v.x;
+  p[8] = s.v.y;
+  p[9] = s.v.z;
+  p[10] = s.w.x;
+  p[11] = s.w.y;
+  p[12] = s.w.z;
+}
+__device__ __forceinline__ bool body_finite(const Body& s) {
+  const float t = s.x.x + s.x.y + s.x.z + s.qw + s.qx + s.qy + s.qz + s.v.x + s.v.y + s.v.z + s.w.x + s.w.y + s.w.z;
+  return fabsf(t) < INFINITY;
+}
+
 // ------------------------------------------------------------------ phase K
 // Kinematic integrator (Algorithm 1, first line): x += h v;
 // q <- normalize(q + h/2 (0, w) (x) q), w in world frame.  Frozen axes hold

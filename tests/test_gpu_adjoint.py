@@ -1,0 +1,190 @@
+"""Parity of the CUDA adjoint with the FP64 oracle adjoint and with FP64
+central finite differences (GPU).
+
+The reverse pass differentiates the FP32 forward trajectory; the oracle's
+tape differentiates the FP64 trajectory from the same FP32-rounded inputs.
+Where a contact, limit or friction decision differs between the two
+trajectories the gradients legitimately differ, so environments whose
+active-contact counts differ are excluded (and counted)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2106_13281_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def brax():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_13281_gb300.system import BraxSystem
+    return BraxSystem
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).cuda()
+
+
+def settled(d, N, seed, drop, T=20):
+    rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
+    rp[:, 2] -= drop
+    st = orc.default_qp(d, N, rp, rr, ang)
+    a = S.actions(d, N, T, seed).astype(np.float64)
+    return orc.rollout(d, st, a).astype(np.float32).astype(np.float64)
+
+
+def gpu_grad(sysm, st, a, gT, gtor, K):
+    out = sysm.rollout(cuda(st), cuda(a), K=K, checkpoints=True, contact_count=True)
+    ga, gs = sysm.rollout_backward(cuda(st), cuda(a), out["checkpoints"], cuda(gT),
+                                   None if gtor is None else cuda(gtor), K=K)
+    sysm.sync_status()
+    return ga.cpu().numpy().astype(np.float64), gs.cpu().numpy().astype(np.float64), out["contact_count"].cpu().numpy()
+
+
+def rel_err(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+
+
+@pytest.mark.parametrize("name,drop,T", [("pendulum", 0.0, 5), ("quadruped", 0.38, 3), ("quadruped", 0.38, 10)])
+def test_adjoint_matches_oracle_tape(brax, name, drop, T):
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    N = 40  # a full group of 32 and a ragged tail
+    st = settled(d, N, 11, drop)
+    a = S.actions(d, N, T, 12).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(13)
+    gT = rng.normal(size=st.shape).astype(np.float32).astype(np.float64)
+    gtor = rng.normal(size=(T, N, 3)).astype(np.float32).astype(np.float64)
+    ga, gs, cc = gpu_grad(sysm, st, a, gT, gtor, K=2)
+    ga_ref, gs_ref = orc.vjp(d, st, a, gT, gtor)
+    _, cc_ref = orc.rollout(d, st, a, contact_count=True)
+    same = cc == cc_ref
+    assert same.mean() >= 0.8
+    errs_a = [rel_err(ga[:, n], ga_ref[:, n]) for n in range(N) if same[n]]
+    errs_s = [rel_err(gs[n], gs_ref[n]) for n in range(N) if same[n]]
+    assert np.median(errs_a) < 1e-3 and np.median(errs_s) < 1e-3, (np.median(errs_a), np.median(errs_s))
+    assert np.mean(np.array(errs_a) < 1e-3) >= 0.9, sorted(errs_a)[-5:]
+    assert np.mean(np.array(errs_s) < 1e-3) >= 0.9, sorted(errs_s)[-5:]
+
+
+def test_adjoint_vs_fp64_central_differences(brax):
+    """Quadruped, 8 envs, 20 steps, loss = -torso x displacement + 1e-3 sum |a|^2:
+    GPU gradients vs FP64 central differences (h = 1e-4) of the oracle, on
+    every entry whose +h and -h runs take the same branches (contact
+    activation, friction stick/slip, limits, clamps) as the unperturbed run;
+    and vs the oracle's tape gradient of the same loss."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 8, 20
+    st = settled(d, N, 21, 0.38)
+    a = S.actions(d, N, T, 22).astype(np.float32).astype(np.float64)
+    gT = np.zeros_like(st)
+    gT[:, 0, 0] = -1.0
+    ga, gs, cc = gpu_grad(sysm, st, a, gT, None, K=5)
+    ga = ga + 2e-3 * a
+    ga_ref, gs_ref = orc.vjp(d, st, a, gT)
+    ga_ref = ga_ref + 2e-3 * a
+    _, cc_ref, sig0 = orc.rollout(d, st, a, contact_count=True, branch_signature=True)
+    same = cc == cc_ref
+    for n in range(N):
+        if same[n]:
+            assert rel_err(ga[:, n], ga_ref[:, n]) < 1e-3 and rel_err(gs[n], gs_ref[n]) < 1e-3, n
+
+    def loss(s0, act):
+        out, sig = orc.rollout(d, s0, act, branch_signature=True)
+        return -(out[:, 0, 0] - s0[:, 0, 0]) + 1e-3 * np.sum(act ** 2, axis=(0, 2)), sig
+
+    rng = np.random.default_rng(23)
+    eps = 1e-4
+    checked = skipped = 0
+    for _ in range(40):
+        t, k = rng.integers(0, T), rng.integers(0, a.shape[2])
+        ap, am = a.copy(), a.copy()
+        ap[t, :, k] += eps
+        am[t, :, k] -= eps
+        lp, sp_ = loss(st, ap)
+        lm, sm_ = loss(st, am)
+        fd = (lp - lm) / (2 * eps)
+        for n in range(N):
+            if not same[n] or sp_[n] != sig0[n] or sm_[n] != sig0[n]:
+                skipped += 1
+                continue
+            g = ga[t, n, k]
+            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-4 * np.abs(ga[:, n]).max(), (t, n, k, fd[n], g)
+            checked += 1
+    assert checked >= 100, (checked, skipped)
+    for _ in range(10):
+        b, j = rng.integers(0, st.shape[1]), rng.choice([0, 1, 2, 7, 8, 9, 10, 11, 12])
+        sp, sm = st.copy(), st.copy()
+        sp[:, b, j] += eps
+        sm[:, b, j] -= eps
+        lp, sp_ = loss(sp, a)
+        lm, sm_ = loss(sm, a)
+        fd = (lp - lm) / (2 * eps)
+        for n in range(N):
+            if not same[n] or sp_[n] != sig0[n] or sm_[n] != sig0[n]:
+                continue
+            g = gs[n, b, j]
+            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-4 * np.abs(gs[n]).max(), (b, j, n, fd[n], g)
+
+
+def test_checkpoint_interval_does_not_change_gradients(brax):
+    """Recomputation from checkpoints is exact: K = 1, 4 and T give bitwise
+    identical gradients (the forward is deterministic)."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 33, 12
+    st = settled(d, N, 31, 0.38)
+    a = S.actions(d, N, T, 32)
+    gT = np.random.default_rng(33).normal(size=st.shape)
+    ref = None
+    for K in (1, 4, T):
+        ga, gs, _ = gpu_grad(sysm, st, a, gT, None, K)
+        if ref is None:
+            ref = (ga, gs)
+        else:
+            assert np.array_equal(ga, ref[0]) and np.array_equal(gs, ref[1])
+
+
+def test_long_rollout_gradients_finite(brax):
+    """1000 steps with checkpoints every 10: the recomputation path runs and
+    the gradients stay finite."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T, K = 64, 1000, 10
+    rp, rr, ang = S.initial_conditions(d, N, 3, height_jitter=0.05)
+    st = orc.default_qp(d, N, rp, rr, ang)
+    a = S.actions(d, N, T, 3)
+    gT = np.zeros_like(st)
+    gT[:, 0, 0] = -1.0
+    ga, gs, _ = gpu_grad(sysm, st, a, gT, None, K)
+    assert np.isfinite(ga).all() and np.isfinite(gs).all()
+    assert np.abs(ga).max() > 0
+
+
+def test_autograd_function(brax):
+    from paper_2106_13281_gb300.autograd import rollout
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 16, 6
+    st = cuda(settled(d, N, 41, 0.38))
+    a = cuda(S.actions(d, N, T, 42)).requires_grad_(True)
+    s0 = st.clone().requires_grad_(True)
+    sT, torso = rollout(sysm, s0, a, K=3)
+    loss = -(sT[:, 0, 0] - s0[:, 0, 0]).sum() + 1e-3 * (a ** 2).sum() + torso[:, :, 2].sum()
+    loss.backward()
+    gT = torch.zeros_like(st)
+    gT[:, 0, 0] = -1.0
+    gtor = torch.zeros((T, N, 3), device="cuda")
+    gtor[:, :, 2] = 1.0
+    out = sysm.rollout(st, a.detach(), K=3, checkpoints=True)
+    ga, gs = sysm.rollout_backward(st, a.detach(), out["checkpoints"], gT, gtor, K=3)
+    assert torch.allclose(a.grad, ga + 2e-3 * a.detach(), atol=1e-6)
+    gs[:, 0, 0] += 1.0
+    assert torch.allclose(s0.grad, gs, atol=1e-6)
