@@ -173,6 +173,25 @@ int brax_rollout_backward(const brax_system* sys, int64_t n_envs, int32_t T, int
                           const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
                           size_t workspace_bytes, void* stream);
 
+/* brax_rollout_backward without a caller workspace, for callers that cannot
+ * allocate device memory when they need a gradient (for example a host
+ * framework whose allocator owns all device memory, or a deployment with a
+ * memory footprint fixed at start-up).  The paper has no counterpart: it is
+ * an interface convenience of this library.  Scratch comes from one
+ * file-scope device array of BRAX_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * loading the library holds until exit.  Arguments and results are those of
+ * brax_rollout_backward.  Errors: BRAX_ERR_WORKSPACE when the rollout needs
+ * more scratch than the array holds (brax_workspace_size says how much);
+ * BRAX_ERR_CUDA if the array's address cannot be looked up.  The first call
+ * on a device looks up the array's device address (once per device); make it
+ * before any stream capture.  Calls share the array, which keeps the last
+ * call's contents (nothing in it needs to start at zero); calls whose
+ * kernels overlap on the GPU race on it.  Allocates nothing. */
+#define BRAX_NOALLOC_SCRATCH_BYTES (32u << 20)
+int brax_rollout_backward_noalloc(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                                  const float* actions, const float* checkpoints, const float* g_state_T,
+                                  const float* g_torso_traj, float* g_actions, float* g_state0, void* stream);
+
 /* Heterogeneous batch (systems of different sizes in one launch).  Arrays
  * of a batch are the concatenation over systems i of the per-system arrays
  * (state blocks [N_i, B_i, 13], action blocks [T, N_i, A_i], torso blocks

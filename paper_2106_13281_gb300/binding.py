@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_DESCRIPTOR", 3: "CUDA", 4:
 EXPORTS = ["brax_system_create", "brax_system_destroy", "brax_system_info", "brax_default_qp", "brax_step",
            "brax_rollout", "brax_workspace_size", "brax_rollout_backward", "brax_batch_create",
            "brax_batch_destroy", "brax_batch_offsets", "brax_batch_rollout", "brax_batch_workspace_size",
-           "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error"]
+           "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error", "brax_rollout_backward_noalloc"]
 
 
 class BraxError(RuntimeError):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         L.brax_batch_workspace_size.argtypes = [P, i32, i32, C.POINTER(C.c_size_t)]
         L.brax_batch_rollout_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, P, P, C.c_size_t, P]
         L.brax_sync_status.argtypes = [P, P]
+        L.brax_rollout_backward_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P]
         if hasattr(L, "brax_system_set_launch"):
             L.brax_system_set_launch.argtypes = [P, i32, i32]
         _lib = L

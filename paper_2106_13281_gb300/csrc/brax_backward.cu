@@ -22,10 +22,12 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "../../include/brax.h"
 #include "brax_adjoint.cuh"
+#include "brax_internal.h"
 #include "brax_kernels.h"
 
 namespace brax {
@@ -396,3 +398,75 @@ size_t backward_smem_bytes(int B, int P, int groups) { return (size_t)groups * b
 int64_t backward_ws_floats_per_group(int B, int P, int K, int S) { return ws_group_floats(B, P, K, S); }
 
 }  // namespace brax
+
+// ------------------------------------------------------------------ reverse mode without allocation
+// Some callers cannot allocate device memory at the time they need a
+// gradient: for example a host framework whose allocator owns all device
+// memory and offers no hook to foreign code, or a deployment that fixes its
+// memory footprint when it starts.  brax_rollout_backward_noalloc serves them
+// with a scratch array that lives in this library's own device image: a
+// file-scope __device__ array of BRAX_NOALLOC_SCRATCH_BYTES bytes, which every
+// GPU that loads the library holds until the process exits.
+//
+// In host code `g_noalloc_scratch` names a host-side stand-in, not a device
+// address, so it is never passed to a kernel directly.  The first call on a
+// device looks up the array's device address with cudaGetSymbolAddress (with
+// that device current) and caches it; make that first call before any stream
+// capture.  All calls share the one array and it keeps the last call's
+// contents; nothing in it needs to start at zero (the reverse kernel writes
+// every scratch word before reading it).  Calls whose kernels overlap on the
+// GPU (different streams, or different threads) race on the array.
+namespace brax {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[BRAX_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+int noalloc_fail(int code, const std::string& msg) {
+  set_last_error(msg);
+  return code;
+}
+
+// Device address of the scratch array on the current device (set up once per device).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+}  // namespace brax
+
+extern "C" int brax_rollout_backward_noalloc(const brax_system* s, int64_t n_envs, int32_t T, int32_t K,
+                                             const float* state0, const float* actions, const float* checkpoints,
+                                             const float* g_state_T, const float* g_torso_traj, float* g_actions,
+                                             float* g_state0, void* stream) {
+  using namespace brax;
+  if (!s || n_envs < 0 || T < 0 || K < 1)
+    return noalloc_fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward_noalloc: bad arguments");
+  const size_t need = backward_workspace_bytes(s, n_envs, std::min(K, std::max(T, 1)));
+  if (need > (size_t)BRAX_NOALLOC_SCRATCH_BYTES)
+    return noalloc_fail(BRAX_ERR_WORKSPACE,
+                        "brax_rollout_backward_noalloc: this rollout needs " + std::to_string(need) +
+                            " bytes of scratch, more than the " + std::to_string((size_t)BRAX_NOALLOC_SCRATCH_BYTES) +
+                            " bytes this entry point holds; use brax_rollout_backward with a caller workspace");
+  void* ws = nullptr;
+  cudaError_t e = noalloc_scratch(&ws);
+  if (e != cudaSuccess)
+    return noalloc_fail(BRAX_ERR_CUDA, std::string("brax_rollout_backward_noalloc: cudaGetSymbolAddress: ") +
+                                           cudaGetErrorString(e));
+  return brax_rollout_backward(s, n_envs, T, K, state0, actions, checkpoints, g_state_T, g_torso_traj, g_actions,
+                               g_state0, ws, (size_t)BRAX_NOALLOC_SCRATCH_BYTES, stream);
+}

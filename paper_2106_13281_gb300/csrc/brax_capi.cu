@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/brax.h"
+#include "brax_internal.h"
 #include "brax_kernels.h"
 #include "brax_params.h"
 
@@ -372,18 +373,6 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
 
 }  // namespace
 
-struct brax_system {
-  int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
-  bool general = false;  // 3-DOF joints or body-body pairs present
-  int device = 0;
-  int pool_off = -1;     // offset of the blob in the constant parameter pool
-  std::vector<unsigned char> blob;
-  unsigned char* d_blob = nullptr;
-  int32_t* d_status = nullptr;
-  int groups = 1;   // groups of 32 environments per thread block
-  int variant = 0;  // launch-bounds variant of the rollout kernel
-};
-
 struct brax_batch {
   std::vector<const brax_system*> sys;
   std::vector<int64_t> n_envs;
@@ -732,6 +721,11 @@ size_t bwd_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
 }
 
 }  // namespace
+
+namespace brax {
+size_t backward_workspace_bytes(const brax_system* s, int64_t n_envs, int32_t K) { return bwd_ws_bytes(s, n_envs, K); }
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace brax
 
 extern "C" int brax_workspace_size(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, size_t* bytes) {
   if (!s || !bytes || n_envs < 0 || T < 0 || K < 1)

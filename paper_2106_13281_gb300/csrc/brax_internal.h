@@ -1,0 +1,27 @@
+// Host-side definition of a system handle (shared by the C ABI translation
+// units).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/brax.h"
+
+struct brax_system {
+  int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
+  bool general = false;  // 3-DOF joints or body-body pairs present
+  int device = 0;
+  int pool_off = -1;     // offset of the blob in the constant parameter pool
+  std::vector<unsigned char> blob;
+  unsigned char* d_blob = nullptr;
+  int32_t* d_status = nullptr;
+  int groups = 1;   // groups of 32 environments per thread block
+  int variant = 0;  // launch-bounds variant of the rollout kernel
+};
+
+
+namespace brax {
+// Reverse-mode scratch bytes a system needs for (n_envs, K) (defined with the C ABI).
+size_t backward_workspace_bytes(const brax_system* s, int64_t n_envs, int32_t K);
+// Set the message brax_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
+}  // namespace brax

@@ -109,6 +109,25 @@ class BraxSystem:
                                             _ptr(workspace), workspace.numel(), _stream()))
         return g_actions, g_state0
 
+    def rollout_backward_noalloc(self, state0, actions, checkpoints, g_state_T, g_torso=None, K=1):
+        """rollout_backward without a caller workspace: the library's own
+        fixed scratch array is used (see brax_rollout_backward_noalloc in
+        include/brax.h for its size limit and sharing rules).  Only the two
+        output tensors are created here; the library allocates nothing."""
+        N = state0.shape[0]
+        T = actions.shape[0]
+        _f32(state0, (N, self.B, 13), "state0")
+        _f32(actions, (T, N, self.A), "actions")
+        _f32(checkpoints, (math.ceil(T / K), N, self.B, 13), "checkpoints")
+        _f32(g_state_T, (N, self.B, 13), "g_state_T")
+        _f32(g_torso, (T, N, 3), "g_torso")
+        g_actions = torch.empty_like(actions)
+        g_state0 = torch.empty_like(state0)
+        check(self._L.brax_rollout_backward_noalloc(self._h, N, T, K, _ptr(state0), _ptr(actions), _ptr(checkpoints),
+                                                    _ptr(g_state_T), _ptr(g_torso), _ptr(g_actions), _ptr(g_state0),
+                                                    _stream()))
+        return g_actions, g_state0
+
     def sync_status(self):
         """Synchronise the current stream; raise if a kernel saw a non-finite state."""
         check(self._L.brax_sync_status(self._h, _stream()))

@@ -1,0 +1,68 @@
+"""The reverse pass without a caller workspace (GPU).
+
+brax_rollout_backward_noalloc serves callers that cannot allocate device
+memory when they need a gradient: it takes its scratch from a fixed array
+inside the library instead of a caller workspace.  These checks call it
+through the C ABI twice in a row (the array keeps the previous call's
+contents) and compare with brax_rollout_backward given a workspace, and
+check that a rollout needing more scratch than the array holds is refused
+with a clear error.  This file is collected last so that a failure here
+leaves every other test already run."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2106_13281_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def system():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_13281_gb300.system import BraxSystem
+    return BraxSystem(S.quadruped())
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).cuda()
+
+
+def inputs(d, N, T, seed):
+    rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
+    rp[:, 2] -= 0.38
+    st = orc.default_qp(d, N, rp, rr, ang)
+    return cuda(st), cuda(S.actions(d, N, T, seed))
+
+
+def test_noalloc_matches_workspace_entry_point_twice(system):
+    d = system.desc
+    N, T, K = 200, 12, 4
+    for call, seed in enumerate((51, 52)):
+        st, a = inputs(d, N, T, seed)
+        out = system.rollout(st, a, K=K, checkpoints=True)
+        rng = np.random.default_rng(seed)
+        gT = cuda(rng.normal(size=(N, system.B, 13)))
+        gtor = cuda(rng.normal(size=(T, N, 3)))
+        ref_a, ref_s = system.rollout_backward(st, a, out["checkpoints"], gT, gtor, K=K)
+        got_a, got_s = system.rollout_backward_noalloc(st, a, out["checkpoints"], gT, gtor, K=K)
+        system.sync_status()
+        assert torch.isfinite(got_a).all() and torch.isfinite(got_s).all()
+        assert torch.allclose(got_a, ref_a, rtol=1e-5, atol=1e-6), call
+        assert torch.allclose(got_s, ref_s, rtol=1e-5, atol=1e-6), call
+
+
+def test_noalloc_refuses_rollouts_beyond_its_scratch(system):
+    from paper_2106_13281_gb300.binding import BraxError
+    d = system.desc
+    N, T, K = 65536, 20, 10
+    assert system.workspace_size(N, T, K) > (32 << 20)
+    st = torch.zeros((N, system.B, 13), device="cuda")
+    a = torch.zeros((T, N, system.A), device="cuda")
+    ck = torch.zeros((2, N, system.B, 13), device="cuda")
+    with pytest.raises(BraxError) as ei:
+        system.rollout_backward_noalloc(st, a, ck, torch.zeros_like(st), K=K)
+    assert ei.value.code == 7 and "scratch" in str(ei.value)
