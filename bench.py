@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--envs", type=int, default=65536)
     p.add_argument("--horizon", type=int, default=1000, help="steps per rollout")
+    p.add_argument("--checkpoint-every", type=int, default=10, help="K of the fwd+bwd figure")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -198,6 +199,40 @@ def run_ours(args):
     h2d = h_state0.numel() * 4 + h_actions.numel() * 4
     d2h = h_out.numel() * 4
 
+    # forward + reverse pass of the same workload (checkpoints every K steps)
+    K = args.checkpoint_every
+    gT = torch.zeros_like(state0)
+    gT[:, 0, 0] = -1.0  # d/dstate_T of -(torso x displacement)
+    ckpt = torch.empty((math.ceil(T / K), N, sysm.B, 13), device="cuda", dtype=torch.float32)
+    ws = torch.empty((sysm.workspace_size(N, T, K),), device="cuda", dtype=torch.uint8)
+    g_actions = torch.empty_like(actions)
+    g_state0 = torch.empty_like(state0)
+    L = sysm._L
+    from paper_2106_13281_gb300.binding import _ptr, check
+
+    def fwd_bwd():
+        check(L.brax_rollout(sysm.handle, N, T, K, _ptr(state0), _ptr(actions), _ptr(state_T), _ptr(ckpt), None, None,
+                             stream.cuda_stream))
+        check(L.brax_rollout_backward(sysm.handle, N, T, K, _ptr(state0), _ptr(actions), _ptr(ckpt), _ptr(gT), None,
+                                      _ptr(g_actions), _ptr(g_state0), _ptr(ws), ws.numel(), stream.cuda_stream))
+
+    fb_steps = max(1, min(args.steps, 3))
+    for _ in range(max(1, min(args.warmup, 2))):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(fb_steps):
+        fwd_bwd()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    sysm.sync_status()
+    fb_ms = barrier_max(f0.elapsed_time(f1), world)
+    fwd_bwd_value = world * envsteps * fb_steps / (fb_ms / 1e3)
+    del ws, ckpt
+
     fl = alg_flops("quadruped")
     flops_per_envstep = fl["flops_per_env_step"]
     achieved_tflops = flops_per_envstep * envsteps / (kern_ms / 1e3) / 1e12
@@ -220,6 +255,9 @@ def run_ours(args):
                    "parallelism": f"env shards x{world}"},
         "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
+        "fwd_bwd": {"value": fwd_bwd_value, "unit": "env-steps/s", "steps": fb_steps, "checkpoint_every": K,
+                    "ms_per_step": fb_ms / fb_steps, "gpu_launches": 2 * fb_steps,
+                    "loss": "-(torso x displacement); gradients w.r.t. the action sequence and the initial state"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": fl.get("traffic_bytes_per_launch"),
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",

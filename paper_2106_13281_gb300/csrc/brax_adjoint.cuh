@@ -337,4 +337,477 @@ __device__ __forceinline__ void joint_hinge_bwd(const JP& bp, const Pub& pp, con
   mulc_bwd(gR, gyc, bp.ac + 3);
 }
 
+// ------------------------------------------------------------------ 3-DOF joint
+// Adjoint of joint_forward() on the 3-DOF path (intrinsic X-Y-Z angles,
+// per-axis limits and actuators about the parent's joint axes, 3-D angular
+// damper, no alignment spring).
+__device__ __forceinline__ void atan2_bwd(float y, float x, float g, float& gy, float& gx) {
+  const float r2 = fmaf(y, y, x * x);
+  const float inv = r2 > 0.f ? __fdividef(1.f, r2) : 0.f;
+  gy += x * inv * g;
+  gx -= y * inv * g;
+}
+
+__device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const Body& s, const Frame& f,
+                                           const float* act, V3 gFc, V3 gTc, V3 gFp, V3 gTp, V3& gx, M3& gR, V3& gv,
+                                           V3& gw, V3& gxp, M3& gRp, V3& gvp, V3& gwp, float* gact) {
+  const V3 rp = mulc(pp.R, bp.off_p);
+  const V3 rc = mulc(f.R, bp.off_c);
+  const V3 dpc = (pp.x + rp) - (s.x + rc);
+  const V3 up = pp.v + cross(pp.w, rp);
+  const V3 uc = s.v + cross(s.w, rc);
+  const V3 F = bp.k * dpc - bp.c * (uc - up);
+  const V3 P[3] = {mulc(pp.R, bp.ap + 0), mulc(pp.R, bp.ap + 3), mulc(pp.R, bp.ap + 6)};
+  const V3 Cc[3] = {mulc(f.R, bp.ac + 0), mulc(f.R, bp.ac + 3), mulc(f.R, bp.ac + 6)};
+  const float m00 = dot(P[0], Cc[0]), m01 = dot(P[0], Cc[1]), m02 = dot(P[0], Cc[2]);
+  const float m12 = dot(P[1], Cc[2]), m22 = dot(P[2], Cc[2]);
+  const float sq = sqrtf(fmaf(m00, m00, m01 * m01));
+  float th[3];
+  th[0] = atan2f(-m12, m22);
+  th[1] = atan2f(m02, sq);
+  th[2] = atan2f(-m01, m00);
+  float L[3];
+  int lim[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    L[a] = 0.f;
+    lim[a] = 0;
+    if (th[a] < bp.lo[a]) {
+      L[a] = bp.kl * (bp.lo[a] - th[a]);
+      lim[a] = 1;
+    } else if (th[a] > bp.hi[a]) {
+      L[a] = bp.kl * (bp.hi[a] - th[a]);
+      lim[a] = 1;
+    }
+    if (bp.act[a] >= 0) L[a] = fmaf(bp.gear[a], clamp1(act[a]), L[a]);
+  }
+  // ---- reverse
+  V3 gF = gFc - gFp;
+  const V3 gtj = gTc - gTp;
+  V3 grc = zero3(), grp = zero3();
+  cross_bwd(rc, F, gTc, grc, gF);
+  cross_bwd(rp, F, -gTp, grp, gF);
+  const V3 gwr = (-bp.ca) * gtj;
+  V3 gP[3], gC[3];
+  float gth[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gP[a] = L[a] * gtj;
+    gC[a] = zero3();
+    const float gL = dot(gtj, P[a]);
+    gth[a] = lim[a] ? -bp.kl * gL : 0.f;
+    if (bp.act[a] >= 0) {
+      const float av = act[a];
+      if (av > -1.f && av < 1.f) gact[a] = fmaf(bp.gear[a], gL, gact[a]);
+    }
+  }
+  float gm00 = 0.f, gm01 = 0.f, gm02 = 0.f, gm12 = 0.f, gm22 = 0.f;
+  {  // th0 = atan2(-m12, m22)
+    float gy = 0.f, gxx = 0.f;
+    atan2_bwd(-m12, m22, gth[0], gy, gxx);
+    gm12 -= gy;
+    gm22 += gxx;
+  }
+  {  // th1 = atan2(m02, sqrt(m00^2 + m01^2))
+    float gy = 0.f, gs = 0.f;
+    atan2_bwd(m02, sq, gth[1], gy, gs);
+    gm02 += gy;
+    if (sq > 0.f) {
+      const float is = __fdividef(1.f, sq);
+      gm00 += gs * m00 * is;
+      gm01 += gs * m01 * is;
+    }
+  }
+  {  // th2 = atan2(-m01, m00)
+    float gy = 0.f, gxx = 0.f;
+    atan2_bwd(-m01, m00, gth[2], gy, gxx);
+    gm01 -= gy;
+    gm00 += gxx;
+  }
+  gP[0] = fma3(gm00, Cc[0], fma3(gm01, Cc[1], fma3(gm02, Cc[2], gP[0])));
+  gP[1] = fma3(gm12, Cc[2], gP[1]);
+  gP[2] = fma3(gm22, Cc[2], gP[2]);
+  gC[0] = gm00 * P[0];
+  gC[1] = gm01 * P[0];
+  gC[2] = fma3(gm02, P[0], fma3(gm12, P[1], gm22 * P[2]));
+  // anchor spring-damper, as in the hinge
+  const V3 gdpc = bp.k * gF;
+  const V3 guc = (-bp.c) * gF;
+  const V3 gup = bp.c * gF;
+  gv = gv + guc;
+  cross_bwd(s.w, rc, guc, gw, grc);
+  gvp = gvp + gup;
+  cross_bwd(pp.w, rp, gup, gwp, grp);
+  gxp = gxp + gdpc;
+  grp = grp + gdpc;
+  gx = gx - gdpc;
+  grc = grc - gdpc;
+  gw = gw + gwr;
+  gwp = gwp - gwr;
+  mulc_bwd(gRp, grp, bp.off_p);
+  mulc_bwd(gR, grc, bp.off_c);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mulc_bwd(gRp, gP[a], bp.ap + 3 * a);
+    mulc_bwd(gR, gC[a], bp.ac + 3 * a);
+  }
+}
+
+// ------------------------------------------------------------------ body-body pairs
+// Adjoint state of one side of a pair (to be added to that body's
+// accumulators through shared-memory atomics).
+struct GSide {
+  V3 x, v, w;
+  M3 R;
+  S6 I;
+};
+__device__ __forceinline__ void zero(GSide& g) {
+  g.x = zero3();
+  g.v = zero3();
+  g.w = zero3();
+  zero(g.R);
+  zero(g.I);
+}
+
+// Closest-point parameters of two segments: adjoint through the branch taken.
+__device__ __forceinline__ void segment_closest_bwd(V3 P1, V3 d1, V3 P2, V3 d2, float gs, float gt, V3& gP1, V3& gd1,
+                                                    V3& gP2, V3& gd2) {
+  const V3 r = P1 - P2;
+  const float a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+  const float tiny = 1e-12f;
+  float ga = 0.f, ge = 0.f, gf = 0.f, gc = 0.f, gb = 0.f;
+  const float c = dot(d1, r);
+  if (a <= tiny && e <= tiny) return;
+  if (a <= tiny) {
+    const float t = __fdividef(f, e);
+    if (t > 0.f && t < 1.f) {
+      gf += __fdividef(gt, e);
+      ge -= gt * __fdividef(t, e);
+    }
+  } else if (e <= tiny) {
+    const float s = __fdividef(-c, a);
+    if (s > 0.f && s < 1.f) {
+      gc -= __fdividef(gs, a);
+      ga -= gs * __fdividef(s, a);
+    }
+  } else {
+    const float b = dot(d1, d2);
+    const float ae = a * e;
+    const float denom = ae - b * b;
+    const bool gen = denom > 1e-5f * ae;
+    const float s0raw = gen ? __fdividef(fmaf(b, f, -c * e), denom) : 0.f;
+    const float s0 = gen ? fminf(fmaxf(s0raw, 0.f), 1.f) : 0.f;
+    const float t0 = __fdividef(fmaf(b, s0, f), e);
+    if (t0 < 0.f) {
+      const float s = __fdividef(-c, a);
+      if (s > 0.f && s < 1.f) {
+        gc -= __fdividef(gs, a);
+        ga -= gs * __fdividef(s, a);
+      }
+    } else if (t0 > 1.f) {
+      const float s = __fdividef(b - c, a);
+      if (s > 0.f && s < 1.f) {
+        const float ia = __fdividef(1.f, a);
+        gb += gs * ia;
+        gc -= gs * ia;
+        ga -= gs * s * ia;
+      }
+    } else {
+      const float ie = __fdividef(1.f, e);
+      gb += gt * s0 * ie;
+      float gs0 = gs + gt * b * ie;
+      gf += gt * ie;
+      ge -= gt * t0 * ie;
+      if (gen && s0raw > 0.f && s0raw < 1.f) {
+        const float id = __fdividef(1.f, denom);
+        const float gnum = gs0 * id;
+        const float gden = -gs0 * s0raw * id;
+        gb += gnum * f;
+        gf += gnum * b;
+        gc -= gnum * e;
+        ge -= gnum * c;
+        ga += gden * e;
+        ge += gden * a;
+        gb -= 2.f * b * gden;
+      }
+    }
+  }
+  gd1 = fma3(2.f * ga, d1, gd1);
+  gd2 = fma3(2.f * ge, d2, gd2);
+  gd2 = fma3(gf, r, gd2);
+  V3 gr = gf * d2;
+  gd1 = fma3(gc, r, gd1);
+  gr = fma3(gc, d1, gr);
+  gd1 = fma3(gb, d2, gd1);
+  gd2 = fma3(gb, d1, gd2);
+  gP1 = gP1 + gr;
+  gP2 = gP2 - gr;
+}
+
+// Reverse of one body-body pair.  Recomputes the detection and the impulse,
+// forms the impulse/contact-point adjoints from both bodies' contact-update
+// adjoints (gacc), and returns the adjoints of both bodies' x1, R, v, w, Ii.
+__device__ __forceinline__ void pair_bwd(const SysP& S, const BodyP* bodies, const PairP& pr, GroupMem& gm,
+                                         const float* gacc, int lane, GSide& GA, GSide& GB) {
+  const Pub A = read_pub(gm, pr.ba, lane);
+  const Pub Bq = read_pub(gm, pr.bb, lane);
+  const V3 P1 = A.x + mulc(A.R, pr.a0);
+  const V3 d1 = mulc(A.R, pr.a1) - mulc(A.R, pr.a0);
+  V3 n, p;
+  float depth = 0.f;
+  bool hit = false;
+  // capsule-capsule intermediates
+  V3 P2 = zero3(), d2 = zero3(), c1 = zero3(), c2 = zero3(), df = zero3();
+  float sp = 0.f, tpar = 0.f, dl = 0.f;
+  // capsule-box intermediates
+  M3 Rb;
+  V3 cb = zero3(), Pl = zero3(), dlv = zero3(), e = zero3(), q = zero3(), nl = zero3(), pl = zero3();
+  float tbox = 0.f, dist = 0.f;
+  int inside = 0, kk = 0;
+  float sgk = 1.f, pen = 0.f;
+  if (pr.type == kCapsuleCapsule) {
+    P2 = Bq.x + mulc(Bq.R, pr.b0);
+    d2 = mulc(Bq.R, pr.b1) - mulc(Bq.R, pr.b0);
+    segment_closest(P1, d1, P2, d2, sp, tpar);
+    c1 = fma3(sp, d1, P1);
+    c2 = fma3(tpar, d2, P2);
+    df = c1 - c2;
+    dl = sqrtf(dot(df, df));
+    depth = pr.ra + pr.rb - dl;
+    if (dl >= S.eps && depth > 0.f) {
+      n = __fdividef(1.f, dl) * df;
+      p = 0.5f * (fma3(-pr.ra, n, c1) + fma3(pr.rb, n, c2));
+      hit = true;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Rb.m[3 * i + j] = fmaf(Bq.R.m[3 * i + 0], pr.bR[0 * 3 + j],
+                               fmaf(Bq.R.m[3 * i + 1], pr.bR[1 * 3 + j], Bq.R.m[3 * i + 2] * pr.bR[2 * 3 + j]));
+    cb = Bq.x + mulc(Bq.R, pr.b0);
+    Pl = mulT(Rb, P1 - cb);
+    dlv = mulT(Rb, d1);
+    const float* he = pr.b1;
+    tbox = seg_box_param(Pl, dlv, he);
+    e = fma3(tbox, dlv, Pl);
+    q = mk3(fminf(fmaxf(e.x, -he[0]), he[0]), fminf(fmaxf(e.y, -he[1]), he[1]), fminf(fmaxf(e.z, -he[2]), he[2]));
+    const V3 dv = e - q;
+    const float d2s = dot(dv, dv);
+    if (d2s > 1e-12f) {
+      dist = sqrtf(d2s);
+      nl = __fdividef(1.f, dist) * dv;
+      depth = pr.ra - dist;
+      pl = 0.5f * (fma3(-pr.ra, nl, e) + q);
+    } else {
+      inside = 1;
+      const float px = he[0] - fabsf(e.x), py = he[1] - fabsf(e.y), pz = he[2] - fabsf(e.z);
+      kk = 0;
+      pen = px;
+      if (py < pen) { pen = py; kk = 1; }
+      if (pz < pen) { pen = pz; kk = 2; }
+      const float ek = kk == 0 ? e.x : (kk == 1 ? e.y : e.z);
+      sgk = ek >= 0.f ? 1.f : -1.f;
+      nl = mk3(kk == 0 ? sgk : 0.f, kk == 1 ? sgk : 0.f, kk == 2 ? sgk : 0.f);
+      depth = pr.ra + pen;
+      pl = fma3(0.5f * (pen - pr.ra), nl, e);
+    }
+    if (depth > 0.f) {
+      n = mul(Rb, nl);
+      p = cb + mul(Rb, pl);
+      hit = true;
+    }
+  }
+  if (!hit) return;
+  const BodyP& ba = bodies[pr.ba];
+  const BodyP& bb = bodies[pr.bb];
+  const S6 Ia = read_pub_Ii(gm, pr.ba, lane);
+  const S6 Ib = read_pub_Ii(gm, pr.bb, lane);
+  const V3 la = p - A.x, lb = p - Bq.x;
+  const V3 u = (A.v + cross(A.w, la)) - (Bq.v + cross(Bq.w, lb));
+  const float kn = eff_mass(ba.flags, ba.inv_mass, Ia, la, n) + eff_mass(bb.flags, bb.inv_mass, Ib, lb, n);
+  if (!(kn > 0.f)) return;
+  const float un = dot(u, n);
+  const float t1 = S.beta_h * depth, t2 = -pr.e * un;
+  const bool first = t1 > t2;
+  const float target = first ? t1 : t2;
+  const float qn = __fdividef(target - un, kn);
+  const bool pos = qn > 0.f;
+  const float jn = pos ? qn : 0.f;
+  V3 J = jn * n;
+  const V3 ut = fma3(-un, n, u);
+  const float ut2 = dot(ut, ut);
+  const bool fric = ut2 > S.eps * S.eps;
+  float rinv = 0.f, utn = 0.f, kt = 1.f, r1 = 0.f, jt = 0.f;
+  bool stick = false;
+  V3 t = zero3();
+  if (fric) {
+    rinv = rsqrtf(ut2);
+    utn = ut2 * rinv;
+    t = rinv * ut;
+    kt = eff_mass(ba.flags, ba.inv_mass, Ia, la, t) + eff_mass(bb.flags, bb.inv_mass, Ib, lb, t);
+    r1 = __fdividef(utn, kt);
+    stick = r1 < pr.mu * jn;
+    jt = stick ? r1 : pr.mu * jn;
+    J = fma3(-jt, t, J);
+  }
+  // ---- adjoints of J and p from the two bodies' velocity-update adjoints
+  V3 gJ = zero3(), gp = zero3();
+  for (int side = 0; side < 2; ++side) {
+    const BodyP& bs = side == 0 ? ba : bb;
+    const int body = side == 0 ? pr.ba : pr.bb;
+    const float sgn = side == 0 ? 1.f : -1.f;
+    const float* ga = gacc + (body * 6) * 32 + lane;
+    V3 gdv = mk3(ga[0], ga[32], ga[64]);
+    V3 gdw = mk3(ga[96], ga[128], ga[160]);
+    if (bs.flags & kAnyFrozen) {
+      gdv = mask3(bs.flags, gdv);
+      gdw = mask3(bs.flags >> 3, gdw);
+    }
+    const S6& I = side == 0 ? Ia : Ib;
+    const V3 x = side == 0 ? A.x : Bq.x;
+    GSide& G = side == 0 ? GA : GB;
+    gJ = fma3(sgn * bs.inv_mass, gdv, gJ);
+    const V3 l = p - x;
+    const V3 lJ = cross(l, J);
+    V3 glJ = zero3();
+    s6_mul_bwd(I, sgn * lJ, gdw, G.I, glJ);
+    glJ = sgn * glJ;
+    V3 gl = zero3();
+    cross_bwd(l, J, glJ, gl, gJ);
+    gp = gp + gl;
+    G.x = G.x - gl;
+  }
+  // ---- response reverse (two bodies)
+  float gjn = dot(gJ, n);
+  V3 gn = jn * gJ;
+  V3 gu = zero3(), gla = zero3(), glb = zero3();
+  float gun = 0.f;
+  if (fric) {
+    const float gjt = -dot(gJ, t);
+    V3 gt = (-jt) * gJ;
+    float gutn = 0.f, gkt = 0.f;
+    if (stick) {
+      gutn = __fdividef(gjt, kt);
+      gkt = -gjt * __fdividef(r1, kt);
+    } else {
+      gjn = fmaf(pr.mu, gjt, gjn);
+    }
+    eff_mass_bwd(ba.flags, ba.inv_mass, Ia, la, t, gkt, gla, gt, GA.I, true);
+    eff_mass_bwd(bb.flags, bb.inv_mass, Ib, lb, t, gkt, glb, gt, GB.I, true);
+    const V3 gut = fma3(gutn, t, rinv * fma3(-dot(t, gt), t, gt));
+    gu = gu + gut;
+    gun -= dot(gut, n);
+    gn = fma3(-un, gut, gn);
+  }
+  float gdepth = 0.f;
+  if (pos) {
+    const float gq = gjn;
+    const float gtarget = __fdividef(gq, kn);
+    gun -= gtarget;
+    const float gkn = -gq * __fdividef(qn, kn);
+    if (first) gdepth = S.beta_h * gtarget;
+    else gun = fmaf(-pr.e, gtarget, gun);
+    eff_mass_bwd(ba.flags, ba.inv_mass, Ia, la, n, gkn, gla, gn, GA.I, true);
+    eff_mass_bwd(bb.flags, bb.inv_mass, Ib, lb, n, gkn, glb, gn, GB.I, true);
+  }
+  gu = fma3(gun, n, gu);
+  gn = fma3(gun, u, gn);
+  GA.v = GA.v + gu;
+  GA.w = GA.w + cross(la, gu);
+  gla = gla + cross(gu, A.w);
+  GB.v = GB.v - gu;
+  GB.w = GB.w - cross(lb, gu);
+  glb = glb - cross(gu, Bq.w);
+  gp = gp + gla + glb;
+  GA.x = GA.x - gla;
+  GB.x = GB.x - glb;
+  // ---- detection reverse
+  V3 gP1 = zero3(), gd1 = zero3();
+  if (pr.type == kCapsuleCapsule) {
+    V3 gc1 = 0.5f * gp, gc2 = 0.5f * gp;
+    gn = fma3(0.5f * (pr.rb - pr.ra), gp, gn);
+    const float idl = __fdividef(1.f, dl);
+    V3 gdf = idl * fma3(-dot(n, gn), n, gn);
+    gdf = fma3(-gdepth, n, gdf);  // depth = ra + rb - |df|
+    gc1 = gc1 + gdf;
+    gc2 = gc2 - gdf;
+    V3 gP2 = gc2, gd2 = tpar * gc2;
+    gP1 = gc1;
+    gd1 = sp * gc1;
+    const float gsp = dot(gc1, d1), gtp = dot(gc2, d2);
+    segment_closest_bwd(P1, d1, P2, d2, gsp, gtp, gP1, gd1, gP2, gd2);
+    GB.x = GB.x + gP2;
+    mulc_bwd(GB.R, gP2, pr.b0);
+    const float db[3] = {pr.b1[0] - pr.b0[0], pr.b1[1] - pr.b0[1], pr.b1[2] - pr.b0[2]};
+    mulc_bwd(GB.R, gd2, db);
+  } else {
+    M3 gRb;
+    zero(gRb);
+    // n = Rb nl, p = cb + Rb pl
+    V3 gnl = mulT(Rb, gn);
+    V3 gpl = mulT(Rb, gp);
+    V3 gcb = gp;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float gni = i == 0 ? gn.x : (i == 1 ? gn.y : gn.z);
+      const float gpi = i == 0 ? gp.x : (i == 1 ? gp.y : gp.z);
+      gRb.m[3 * i + 0] += gni * nl.x + gpi * pl.x;
+      gRb.m[3 * i + 1] += gni * nl.y + gpi * pl.y;
+      gRb.m[3 * i + 2] += gni * nl.z + gpi * pl.z;
+    }
+    V3 ge = zero3();
+    const float* he = pr.b1;
+    if (!inside) {
+      ge = 0.5f * gpl;
+      gnl = fma3(-0.5f * pr.ra, gpl, gnl);
+      V3 gq = 0.5f * gpl;
+      const float idist = __fdividef(1.f, dist);
+      V3 gdv = idist * fma3(-dot(nl, gnl), nl, gnl);
+      gdv = fma3(-gdepth, nl, gdv);  // depth = ra - |dv|
+      ge = ge + gdv;
+      gq = gq - gdv;
+      ge.x += (e.x > -he[0] && e.x < he[0]) ? gq.x : 0.f;
+      ge.y += (e.y > -he[1] && e.y < he[1]) ? gq.y : 0.f;
+      ge.z += (e.z > -he[2] && e.z < he[2]) ? gq.z : 0.f;
+    } else {
+      ge = gpl;
+      const float gpen = 0.5f * dot(gpl, nl) + gdepth;
+      if (kk == 0) ge.x -= sgk * gpen;
+      else if (kk == 1) ge.y -= sgk * gpen;
+      else ge.z -= sgk * gpen;
+    }
+    // e = Pl + t dl (t fixed)
+    const V3 gPl = ge, gdl = tbox * ge;
+    // Pl = Rb^T (P1 - cb), dl = Rb^T d1
+    const V3 x1 = P1 - cb;
+    const V3 gx1 = mul(Rb, gPl);
+    gP1 = gx1;
+    gcb = gcb - gx1;
+    gd1 = mul(Rb, gdl);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float xi = i == 0 ? x1.x : (i == 1 ? x1.y : x1.z);
+      const float di = i == 0 ? d1.x : (i == 1 ? d1.y : d1.z);
+      gRb.m[3 * i + 0] += xi * gPl.x + di * gdl.x;
+      gRb.m[3 * i + 1] += xi * gPl.y + di * gdl.y;
+      gRb.m[3 * i + 2] += xi * gPl.z + di * gdl.z;
+    }
+    // Rb = R_b bR: gR_b += gRb bR^T ; cb = x_b + R_b b0
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        GB.R.m[3 * i + k] += gRb.m[3 * i + 0] * pr.bR[3 * k + 0] + gRb.m[3 * i + 1] * pr.bR[3 * k + 1] +
+                             gRb.m[3 * i + 2] * pr.bR[3 * k + 2];
+    GB.x = GB.x + gcb;
+    mulc_bwd(GB.R, gcb, pr.b0);
+  }
+  GA.x = GA.x + gP1;
+  mulc_bwd(GA.R, gP1, pr.a0);
+  const float da[3] = {pr.a1[0] - pr.a0[0], pr.a1[1] - pr.a0[1], pr.a1[2] - pr.a0[2]};
+  mulc_bwd(GA.R, gd1, da);
+}
+
 }  // namespace brax

@@ -140,6 +140,7 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   const int np = bp.n_points;
   if (kGeneral) {
     for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+    for (int k = b; k < S.P; k += B) pair_forward(S, bodies, pairs[k], gm, k, lane);
   } else {
     if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
     if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
@@ -147,6 +148,10 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   }
   group_sync(bar, nthr);
   // ---- forward values of phase P
+  int n_pair = 0;
+  if (kGeneral)
+    for (int i = 0; i < bp.n_bpairs; ++i)
+      if (gm.slotf(bp.bpair[i] >> 1, 6)[lane] != 0.f) ++n_pair;
   V3 Ft = wr.F, Tt = wr.tau;
   for (int c = 0; c < bp.n_children; ++c) {
     const float* r = gm.reactf(bp.children[c], 0) + lane;
@@ -154,7 +159,7 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     Tt = Tt + mk3(r[96], r[128], r[160]);
   }
   // ---- reverse P: potential and collision integrators
-  const int n = acc.n;
+  const int n = acc.n + n_pair;
   const float inv = n > 0 ? ((S.average && n > 1) ? __fdividef(1.f, (float)n) : 1.f) : 0.f;
   const V3 gdv = inv * g.v, gdw = inv * g.w;
   V3 gv2 = g.v, gw2 = g.w;
@@ -177,6 +182,15 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     o[128] = gTt.y;
     o[160] = gTt.z;
   }
+  if (kGeneral && (bp.flags & kInPair)) {
+    float* o = bm.gacc + (b * 6) * 32 + lane;
+    o[0] = gdv.x;
+    o[32] = gdv.y;
+    o[64] = gdv.z;
+    o[96] = gdw.x;
+    o[128] = gdw.y;
+    o[160] = gdw.z;
+  }
   group_sync(bar, nthr);
   // ---- reverse J
   V3 gx1 = g.x;
@@ -189,8 +203,12 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     V3 gxp = zero3(), gvp = zero3(), gwp = zero3();
     M3 gRp;
     zero(gRp);
-    if (kGeneral) joint_hinge_bwd(bp, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
-    else joint_hinge_bwd(hr, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    if (!kGeneral)
+      joint_hinge_bwd(hr, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    else if (bp.dof == 1)
+      joint_hinge_bwd(bp, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    else
+      joint3_bwd(bp, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
     float* o = bm.gpub + (b * 18) * 32 + lane;
     o[0] = gxp.x;
     o[32] = gxp.y;
@@ -215,6 +233,34 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
         plane_point_bwd(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
     }
   }
+  if (kGeneral) {
+    for (int k = b; k < S.P; k += B) {
+      const PairP& prk = pairs[k];
+      if (gm.slotf(k, 6)[lane] == 0.f) continue;
+      GSide GA, GB;
+      zero(GA);
+      zero(GB);
+      pair_bwd(S, bodies, prk, gm, bm.gacc, lane, GA, GB);
+      for (int side = 0; side < 2; ++side) {
+        const int body = side == 0 ? prk.ba : prk.bb;
+        GSide& G = side == 0 ? GA : GB;
+        const Pub X = read_pub(gm, body, lane);
+        inv_inertia_bwd(X.R, bodies[body].inv_I, G.I, G.R);
+        float* o = bm.gpair + (body * 18) * 32 + lane;
+        atomicAdd(o + 0 * 32, G.x.x);
+        atomicAdd(o + 1 * 32, G.x.y);
+        atomicAdd(o + 2 * 32, G.x.z);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) atomicAdd(o + (3 + i) * 32, G.R.m[i]);
+        atomicAdd(o + 12 * 32, G.v.x);
+        atomicAdd(o + 13 * 32, G.v.y);
+        atomicAdd(o + 14 * 32, G.v.z);
+        atomicAdd(o + 15 * 32, G.w.x);
+        atomicAdd(o + 16 * 32, G.w.y);
+        atomicAdd(o + 17 * 32, G.w.z);
+      }
+    }
+  }
   group_sync(bar, nthr);
   // ---- reverse K: gather children's adjoints of this body, frame, kinematic
   for (int c = 0; c < bp.n_children; ++c) {
@@ -224,6 +270,16 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     for (int i = 0; i < 9; ++i) gR.m[i] += o[(3 + i) * 32];
     gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
     gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
+  }
+  if (kGeneral && (bp.flags & kInPair)) {
+    float* o = bm.gpair + (b * 18) * 32 + lane;
+    gx1 = gx1 + mk3(o[0], o[32], o[64]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gR.m[i] += o[(3 + i) * 32];
+    gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
+    gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
+#pragma unroll
+    for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
   inv_inertia_bwd(f.R, bp.inv_I, gI, gR);
   float gq1[4] = {g.q[0], g.q[1], g.q[2], g.q[3]};
@@ -273,6 +329,11 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
     if (bp.flags & kHasParent) hr = hinge_regs(bp);
     if (bp.n_points > 0) pr[0] = point_regs(bp.pt[0]);
     if (bp.n_points > 1) pr[1] = point_regs(bp.pt[1]);
+  }
+  if (kGeneral && P > 0) {
+    float* o = bm.gpair + (b * 18) * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
   GBody gs = zero_gbody();
   if (valid) {

@@ -699,21 +699,6 @@ namespace {
 // One group of 32 environments per block for the reverse kernel.
 int64_t bwd_groups_total(int64_t n_envs) { return (n_envs + 31) / 32; }
 
-int check_bwd_system(const brax_system* s) {
-  if (s->general) {
-    const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
-    if (S->P > 0)
-      return fail(BRAX_ERR_INVALID_ARGUMENT,
-                  "reverse mode: systems with body-body collision pairs are not supported by this build");
-    for (int b = 0; b < s->B; ++b) {
-      const BodyP* bp = reinterpret_cast<const BodyP*>(s->blob.data() + blob_bodies_off()) + b;
-      if (bp->dof == 3)
-        return fail(BRAX_ERR_INVALID_ARGUMENT, "reverse mode: 3-DOF joints are not supported by this build");
-    }
-  }
-  return BRAX_OK;
-}
-
 size_t bwd_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
   const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
   return (size_t)bwd_groups_total(n_envs) * (size_t)backward_ws_floats_per_group(s->B, s->P, K, S->substeps) *
@@ -739,8 +724,6 @@ extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32
                                      const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
                                      size_t workspace_bytes, void* stream) {
   if (!s || n_envs < 0 || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: bad arguments");
-  int rc = check_bwd_system(s);
-  if (rc != BRAX_OK) return rc;
   if (n_envs == 0) return BRAX_OK;
   if (!g_state_T) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: g_state_T is required");
   cudaStream_t st = as_stream(stream);

@@ -437,3 +437,26 @@ def actions(desc, n_envs, T, seed, low=-1.0, high=1.0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed + 7919))
     A = len(desc["gear"])
     return rng.uniform(low, high, size=(T, n_envs, A)).astype(np.float32)
+
+
+def capsule_on_box(inside=False) -> dict:
+    """Test scene for capsule-box contact: a 0.1 m box (mass 0.5) on the plane
+    and a free capsule (r 0.04, len 0.3, mass 0.3) lying across its top
+    face, tilted; with `inside` the capsule starts with its segment inside
+    the box (the deep-penetration branch)."""
+    sb = SceneBuilder(dt=0.05, substeps=10, gravity=(0, 0, -9.81))
+    half = (0.05, 0.05, 0.05)
+    box = sb.body("box", 0.5, box_inertia(0.5, half), (0.0, 0.0, 0.05))
+    bc = sb.collider(box, BOX, half=half, friction=1.0)
+    z = 0.06 if inside else 0.135
+    axis = np.array([1.0, 0.3, 0.15])
+    cap = sb.capsule_body("rod", 0.3, 0.04, 0.3, (0.02, 0.01, z), axis / np.linalg.norm(axis))
+    ground = sb.plane(friction=1.0)
+    sb.pair(bc, ground)
+    sb.pair(sb.collider_of(cap), ground)
+    sb.pair(sb.collider_of(cap), bc)
+    return sb.build()
+
+
+SCENES["capsule_on_box"] = lambda joint=None: capsule_on_box(False)
+SCENES["capsule_in_box"] = lambda joint=None: capsule_on_box(True)
