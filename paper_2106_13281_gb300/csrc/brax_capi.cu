@@ -770,12 +770,44 @@ extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_backward");
 }
 
+namespace {
+// Reverse-mode layout of a batch: one launch, system i's blocks hold G_i
+// groups of 32 environments, its workspace block starts at ws_off[i].
+struct BwdBatchPlan {
+  int grid = 0, threads = 0;
+  size_t smem = 0, ws_bytes = 0;
+  bool general = false;
+  std::vector<int> groups, cta_begin, cta_end;
+  std::vector<size_t> ws_off;
+};
+BwdBatchPlan plan_batch_backward(const brax_batch* b, int32_t K) {
+  BwdBatchPlan pl;
+  pl.threads = 32 * b->warps;
+  int cta = 0;
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    const brax_system* s = b->sys[i];
+    const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
+    const int G = batch_groups(s, b->warps);
+    const int64_t per = 32LL * G;
+    const int nb = (int)((b->n_envs[i] + per - 1) / per);
+    pl.groups.push_back(G);
+    pl.cta_begin.push_back(cta);
+    pl.cta_end.push_back(cta + nb);
+    cta += nb;
+    pl.ws_off.push_back(pl.ws_bytes);
+    const size_t wb = (size_t)nb * G * (size_t)backward_ws_floats_per_group(s->B, s->P, K, S->substeps) * sizeof(float);
+    pl.ws_bytes += (wb + 255) & ~size_t(255);
+    pl.smem = std::max(pl.smem, backward_smem_bytes(s->B, s->P, G));
+    pl.general = pl.general || s->general;
+  }
+  pl.grid = cta;
+  return pl;
+}
+}  // namespace
+
 extern "C" int brax_batch_workspace_size(const brax_batch* b, int32_t T, int32_t K, size_t* bytes) {
   if (!b || !bytes || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_workspace_size: bad arguments");
-  size_t tot = 0;
-  for (size_t i = 0; i < b->sys.size(); ++i)
-    tot += (bwd_ws_bytes(b->sys[i], b->n_envs[i], std::min(K, std::max(T, 1))) + 255) & ~size_t(255);
-  *bytes = tot;
+  *bytes = plan_batch_backward(b, std::min(K, std::max(T, 1))).ws_bytes;
   return BRAX_OK;
 }
 
@@ -783,25 +815,48 @@ extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32
                                            const float* actions, const float* checkpoints, const float* g_state_T,
                                            const float* g_torso_traj, float* g_actions, float* g_state0,
                                            void* workspace, size_t workspace_bytes, void* stream) {
-  if (!b || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: bad arguments");
-  size_t need = 0;
-  brax_batch_workspace_size(b, T, K, &need);
-  if (T > 0 && (!workspace || workspace_bytes < need))
-    return fail(BRAX_ERR_WORKSPACE, "brax_batch_rollout_backward: workspace missing or too small");
-  // one launch per system of the batch, all on the same stream
-  size_t ws_off = 0;
-  for (size_t i = 0; i < b->sys.size(); ++i) {
-    int64_t so, ao, to, co;
-    brax_batch_offsets(b, T, K, (int32_t)i, &so, &ao, &to, &co);
-    const brax_system* s = b->sys[i];
-    const size_t wb = bwd_ws_bytes(s, b->n_envs[i], std::min(K, std::max(T, 1)));
-    int rc = brax_rollout_backward(s, b->n_envs[i], T, K, state0 + so, actions ? actions + ao : nullptr,
-                                   checkpoints ? checkpoints + co : nullptr, g_state_T + so,
-                                   g_torso_traj ? g_torso_traj + to : nullptr, g_actions ? g_actions + ao : nullptr,
-                                   g_state0 ? g_state0 + so : nullptr,
-                                   workspace ? reinterpret_cast<char*>(workspace) + ws_off : nullptr, wb, stream);
-    if (rc != BRAX_OK) return rc;
-    ws_off += (wb + 255) & ~size_t(255);
+  if (!b || T < 0 || K < 1 || !g_state_T)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: bad arguments");
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (g_state0) {
+      int64_t tot = 0;
+      for (size_t i = 0; i < b->sys.size(); ++i) tot += b->n_envs[i] * b->sys[i]->B * 13;
+      cudaError_t e = cudaMemcpyAsync(g_state0, g_state_T, (size_t)tot * sizeof(float), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "brax_batch_rollout_backward");
+    }
+    return BRAX_OK;
   }
-  return BRAX_OK;
+  if (!state0 || !checkpoints) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: null inputs");
+  const BwdBatchPlan pl = plan_batch_backward(b, std::min(K, T));
+  if (!workspace || workspace_bytes < pl.ws_bytes)
+    return fail(BRAX_ERR_WORKSPACE, "brax_batch_rollout_backward: workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(BRAX_ERR_WORKSPACE, "brax_batch_rollout_backward: workspace must be 256-byte aligned");
+  if (pl.grid == 0) return BRAX_OK;
+  Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_segs = (int)b->sys.size();
+  L.T = T;
+  L.K = K;
+  for (int i = 0; i < L.n_segs; ++i) {
+    int64_t so, ao, to, co;
+    brax_batch_offsets(b, T, K, i, &so, &ao, &to, &co);
+    Seg sg = make_seg(b->sys[i], pl.groups[i], b->n_envs[i]);
+    sg.cta_begin = pl.cta_begin[i];
+    sg.cta_end = pl.cta_end[i];
+    sg.state0 = state0 + so;
+    sg.actions = actions ? actions + ao : nullptr;
+    sg.ckpt = const_cast<float*>(checkpoints) + co;
+    sg.g_state_T = g_state_T + so;
+    sg.g_torso = g_torso_traj ? g_torso_traj + to : nullptr;
+    sg.g_actions = g_actions ? g_actions + ao : nullptr;
+    sg.g_state0 = g_state0 ? g_state0 + so : nullptr;
+    sg.ws = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + pl.ws_off[i]);
+    L.seg[i] = sg;
+  }
+  const int variant = pick_variant(pl.threads);
+  if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: block too large");
+  cudaError_t e = launch_rollout_backward(L, pl.grid, pl.threads, pl.smem, variant, pl.general, st);
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout_backward");
 }

@@ -131,3 +131,71 @@ class BraxSystem:
     def sync_status(self):
         """Synchronise the current stream; raise if a kernel saw a non-finite state."""
         check(self._L.brax_sync_status(self._h, _stream()))
+
+
+class BraxBatch:
+    """Systems of different sizes stepped in one launch (forward and reverse).
+
+    Arrays are concatenations over systems of the per-system arrays: state
+    blocks [N_i, B_i, 13], action blocks [T, N_i, A_i], torso blocks
+    [T, N_i, 3], checkpoint blocks [ceil(T/K), N_i, B_i, 13].
+    """
+
+    def __init__(self, systems, n_envs):
+        L = load_library()
+        self._L = L
+        self.systems = list(systems)
+        self.n_envs = [int(n) for n in n_envs]
+        arr = (C.c_void_p * len(self.systems))(*[s.handle.value for s in self.systems])
+        ns = (C.c_int64 * len(self.systems))(*self.n_envs)
+        h = C.c_void_p()
+        check(L.brax_batch_create(arr, ns, len(self.systems), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.brax_batch_destroy(h)
+            self._h = None
+
+    def sizes(self, T, K=1):
+        """Total elements of the state, action, torso and checkpoint arrays."""
+        st = sum(n * s.B * 13 for s, n in zip(self.systems, self.n_envs))
+        ac = sum(T * n * s.A for s, n in zip(self.systems, self.n_envs))
+        to = sum(T * n * 3 for n in self.n_envs)
+        ck = sum(math.ceil(T / K) * n * s.B * 13 for s, n in zip(self.systems, self.n_envs))
+        return st, ac, to, ck
+
+    def offsets(self, T, K, i):
+        o = [C.c_int64() for _ in range(4)]
+        check(self._L.brax_batch_offsets(self._h, T, K, i, *[C.byref(x) for x in o]))
+        return tuple(x.value for x in o)
+
+    def rollout(self, state0, actions, T, K=1, checkpoints=False, torso=False):
+        st_n, ac_n, to_n, ck_n = self.sizes(T, K)
+        if state0.numel() != st_n or actions.numel() != ac_n:
+            raise ValueError("batch arrays do not match the systems' sizes")
+        out = {"state_T": torch.empty_like(state0)}
+        if checkpoints:
+            out["checkpoints"] = torch.empty((ck_n,), device="cuda", dtype=torch.float32)
+        if torso:
+            out["torso"] = torch.empty((to_n,), device="cuda", dtype=torch.float32)
+        check(self._L.brax_batch_rollout(self._h, T, K, _ptr(state0), _ptr(actions), _ptr(out["state_T"]),
+                                         _ptr(out.get("checkpoints")), _ptr(out.get("torso")), _stream()))
+        return out
+
+    def workspace_size(self, T, K):
+        b = C.c_size_t()
+        check(self._L.brax_batch_workspace_size(self._h, T, K, C.byref(b)))
+        return b.value
+
+    def rollout_backward(self, state0, actions, checkpoints, g_state_T, T, K=1, g_torso=None, workspace=None):
+        nbytes = self.workspace_size(T, K)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty((max(nbytes, 1),), device="cuda", dtype=torch.uint8)
+        g_actions = torch.empty_like(actions)
+        g_state0 = torch.empty_like(state0)
+        check(self._L.brax_batch_rollout_backward(self._h, T, K, _ptr(state0), _ptr(actions), _ptr(checkpoints),
+                                                  _ptr(g_state_T), _ptr(g_torso), _ptr(g_actions), _ptr(g_state0),
+                                                  _ptr(workspace), workspace.numel(), _stream()))
+        return g_actions, g_state0

@@ -1,0 +1,114 @@
+"""Heterogeneous batch (GPU): systems of different sizes (pendulum, quadruped,
+biped, arm + box) in one forward launch and one reverse launch; each
+system's slice equals its solo launch, and the batch is captured in a CUDA
+graph."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc
+from paper_2106_13281_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["pendulum", "quadruped", "biped", "arm_box"]
+
+
+@pytest.fixture(scope="module")
+def batch_setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_13281_gb300.system import BraxBatch, BraxSystem
+    descs = [S.SCENES[n]() for n in NAMES]
+    systems = [BraxSystem(d) for d in descs]
+    n_envs = [40, 70, 33, 45]
+    return descs, systems, n_envs, BraxBatch(systems, n_envs)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).cuda()
+
+
+def make_inputs(descs, n_envs, T, seed):
+    states, acts = [], []
+    for i, (d, n) in enumerate(zip(descs, n_envs)):
+        rp, rr, ang = S.initial_conditions(d, n, seed + i, height_jitter=0.05)
+        if NAMES[i] == "quadruped":
+            rp[:, 2] -= 0.38
+        states.append(orc.default_qp(d, n, rp, rr, ang).astype(np.float32))
+        acts.append(S.actions(d, n, T, seed + i))
+    return states, acts
+
+
+def cat(arrs):
+    return cuda(np.concatenate([a.reshape(-1) for a in arrs]))
+
+
+def test_batch_forward_matches_solo(batch_setup):
+    descs, systems, n_envs, batch = batch_setup
+    T, K = 6, 4
+    states, acts = make_inputs(descs, n_envs, T, 71)
+    out = batch.rollout(cat(states), cat(acts), T, K=K, checkpoints=True, torso=True)
+    for i, s in enumerate(systems):
+        so, ao, to, co = batch.offsets(T, K, i)
+        n = n_envs[i]
+        solo = s.rollout(cuda(states[i]), cuda(acts[i]), K=K, checkpoints=True, torso=True)
+        got = out["state_T"][so:so + n * s.B * 13].view(n, s.B, 13)
+        assert torch.allclose(got, solo["state_T"], rtol=1e-6, atol=1e-6), NAMES[i]
+        tor = out["torso"][to:to + T * n * 3].view(T, n, 3)
+        assert torch.allclose(tor, solo["torso"], rtol=1e-6, atol=1e-6)
+        nck = math.ceil(T / K)
+        ck = out["checkpoints"][co:co + nck * n * s.B * 13].view(nck, n, s.B, 13)
+        assert torch.allclose(ck, solo["checkpoints"], rtol=1e-6, atol=1e-6)
+        s.sync_status()
+
+
+def test_batch_backward_matches_solo(batch_setup):
+    descs, systems, n_envs, batch = batch_setup
+    T, K = 5, 2
+    states, acts = make_inputs(descs, n_envs, T, 81)
+    rng = np.random.default_rng(82)
+    gTs = [rng.normal(size=st.shape).astype(np.float32) for st in states]
+    out = batch.rollout(cat(states), cat(acts), T, K=K, checkpoints=True)
+    ga, gs = batch.rollout_backward(cat(states), cat(acts), out["checkpoints"], cat(gTs), T, K=K)
+    for i, s in enumerate(systems):
+        so, ao, to, co = batch.offsets(T, K, i)
+        n = n_envs[i]
+        solo = s.rollout(cuda(states[i]), cuda(acts[i]), K=K, checkpoints=True)
+        ra, rs = s.rollout_backward(cuda(states[i]), cuda(acts[i]), solo["checkpoints"], cuda(gTs[i]), K=K)
+        got_s = gs[so:so + n * s.B * 13].view(n, s.B, 13)
+        got_a = ga[ao:ao + T * n * s.A].view(T, n, s.A)
+        scale = rs.abs().max().item() + 1.0
+        assert torch.allclose(got_s, rs, rtol=1e-4, atol=1e-5 * scale), NAMES[i]
+        if s.A:
+            assert torch.allclose(got_a, ra, rtol=1e-4, atol=1e-5 * (ra.abs().max().item() + 1.0)), NAMES[i]
+
+
+def test_batch_cuda_graph(batch_setup):
+    """Forward and reverse of the batch captured in one CUDA graph replay the
+    eager results."""
+    descs, systems, n_envs, batch = batch_setup
+    T, K = 4, 2
+    states, acts = make_inputs(descs, n_envs, T, 91)
+    s0, a0 = cat(states), cat(acts)
+    st_n, ac_n, to_n, ck_n = batch.sizes(T, K)
+    gT = torch.ones_like(s0)
+    ws = torch.empty((batch.workspace_size(T, K),), device="cuda", dtype=torch.uint8)
+    eager = batch.rollout(s0, a0, T, K=K, checkpoints=True)
+    e_ga, e_gs = batch.rollout_backward(s0, a0, eager["checkpoints"], gT, T, K=K, workspace=ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            out = batch.rollout(s0, a0, T, K=K, checkpoints=True)
+            ga, gs = batch.rollout_backward(s0, a0, out["checkpoints"], gT, T, K=K, workspace=ws)
+    torch.cuda.current_stream().wait_stream(stream)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out["state_T"], eager["state_T"])
+    assert torch.equal(gs, e_gs) and torch.equal(ga, e_ga)
