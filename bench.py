@@ -118,13 +118,25 @@ def dist_setup(n_gpus):
 
 
 def barrier_max(x, world):
+    """Maximum of a per-rank time over all ranks (timing only; no data-path collective)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_seed(rank):
+    """Each rank simulates its own shard of environments (weak scaling)."""
+    return 1 + 1000 * rank
+
+
+def aggregate_rate(world, envs_per_rank, steps_per_rollout, rollouts, max_ms):
+    """Whole-job env-steps/s: every rank's env-steps over the slowest rank's time."""
+    return world * envs_per_rank * steps_per_rollout * rollouts / (max_ms / 1e3)
 
 
 def run_ours(args):
@@ -138,7 +150,7 @@ def run_ours(args):
     N, T = args.envs, args.horizon
     d = S.quadruped()
     sysm = BraxSystem(d)
-    seed = 1 + 1000 * rank  # each rank simulates its own shard of environments
+    seed = shard_seed(rank)
     rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
     state0 = sysm.default_qp(N, f32(rp), f32(rr), f32(ang))
@@ -170,7 +182,7 @@ def run_ours(args):
     total_ms = barrier_max(start.elapsed_time(end), world)
     kern_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
     envsteps = N * T
-    value = world * envsteps * args.steps / (total_ms / 1e3)
+    value = aggregate_rate(world, N, T, args.steps, total_ms)
 
     # end to end through the public API: pinned host inputs in, state back out, every step
     h_state0 = state0.cpu().pin_memory()
@@ -195,7 +207,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = barrier_max(e0.elapsed_time(e1), world)
-    e2e_value = world * envsteps * args.steps / (e2e_ms / 1e3)
+    e2e_value = aggregate_rate(world, N, T, args.steps, e2e_ms)
     h2d = h_state0.numel() * 4 + h_actions.numel() * 4
     d2h = h_out.numel() * 4
 
@@ -230,7 +242,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     sysm.sync_status()
     fb_ms = barrier_max(f0.elapsed_time(f1), world)
-    fwd_bwd_value = world * envsteps * fb_steps / (fb_ms / 1e3)
+    fwd_bwd_value = aggregate_rate(world, N, T, fb_steps, fb_ms)
     del ws, ckpt
 
     fl = alg_flops("quadruped")
