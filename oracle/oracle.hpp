@@ -384,6 +384,7 @@ template <class T> inline void segment_closest(const V3<T>& P1, const V3<T>& d1,
   if (val(denom) > 1e-5 * val(ae)) s = vclamp((b * f - cc * e) / denom, 0.0, 1.0);
   else s = T(0.0);
   t = (b * s + f) / e;
+  note_branch(60 + (val(t) < 0.0 ? 1 : (val(t) > 1.0 ? 2 : 0)) + (val(denom) > 1e-5 * val(ae) ? 4 : 0));
   if (val(t) < 0.0) {
     t = T(0.0);
     s = vclamp(-cc / a, 0.0, 1.0);
@@ -391,6 +392,9 @@ template <class T> inline void segment_closest(const V3<T>& P1, const V3<T>& d1,
     t = T(1.0);
     s = vclamp((b - cc) / a, 0.0, 1.0);
   }
+  // which parameters ended on an end point of their segment (clamped)
+  note_branch(100 + (val(s) == 0.0 ? 1 : 0) + (val(s) == 1.0 ? 2 : 0) + (val(t) == 0.0 ? 4 : 0) +
+              (val(t) == 1.0 ? 8 : 0));
 }
 
 // Capsule geometry: `length` is the total tip-to-tip length (READING); the
@@ -420,49 +424,86 @@ template <class T> inline void sphere_plane(const V3<T>& e, double r, const doub
   if (val(depth) > 0.0) out.push_back(Contact<T>{N, e - T(r) * N, depth, body, -1, mu, el});
 }
 
-// Golden-section minimisation of the squared distance from a segment to an
-// axis-aligned box (box frame).  READING: the distance is convex in the
-// segment parameter; 24 golden-section iterations with one new evaluation per
-// iteration; the parameter is a value decision (zero derivative).
+// Exact minimiser of the squared distance from the segment Pl + t dl,
+// t in [0, 1], to the axis-aligned box |x_i| <= he_i (box frame).
+// READING: the squared distance is a convex piecewise quadratic in t whose
+// pieces end where a coordinate crosses a face plane (t = (+-he_i - Pl_i) /
+// dl_i).  Each piece is minimised in closed form (its stationary point,
+// clamped to the piece) and the smallest value wins; where a piece is flat
+// (no active coordinate, or the segment parallel to the active faces) its
+// midpoint is taken.  The parameter is a value decision (zero derivative).
 template <class T> inline double seg_box_param(const V3<T>& Pl, const V3<T>& dl, const double* he) {
-  auto f = [&](double t) {
-    V3<T> e = Pl + T(t) * dl;
-    T r[3] = {e.x, e.y, e.z};
-    T acc(0.0);
+  const double P[3] = {val(Pl.x), val(Pl.y), val(Pl.z)};
+  const double D[3] = {val(dl.x), val(dl.y), val(dl.z)};
+  // The search runs in plain doubles (its result carries no derivative); its
+  // arithmetic is still counted: 7 flops per coordinate of one distance.
+  auto d2 = [&](double t) {
+    count_flop(21);
+    double acc = 0.0;
     for (int i = 0; i < 3; ++i) {
-      T q = vclamp(r[i], -he[i], he[i]);
-      T d = r[i] - q;
-      acc = acc + d * d;
+      const double e = P[i] + t * D[i];
+      const double r = e - std::min(std::max(e, -he[i]), he[i]);
+      acc += r * r;
     }
-    return val(acc);
+    return acc;
   };
-  const double rho = 0.5 * (std::sqrt(5.0) - 1.0);
-  double a = 0.0, b = 1.0;
-  double c = b - rho * (b - a), d = a + rho * (b - a);
-  double fc = f(c), fd = f(d);
-  for (int it = 0; it < 24; ++it) {
-    if (fc < fd) {
-      b = d;
-      d = c;
-      fd = fc;
-      c = b - rho * (b - a);
-      fc = f(c);
-    } else {
-      a = c;
-      c = d;
-      fc = fd;
-      d = a + rho * (b - a);
-      fd = f(d);
+  std::vector<double> knots = {0.0, 1.0};
+  for (int i = 0; i < 3; ++i) {
+    if (D[i] == 0.0) continue;
+    for (double face : {-he[i], he[i]}) {
+      const double t = (face - P[i]) / D[i];
+      count_flop(2);
+      if (t > 0.0 && t < 1.0) knots.push_back(t);
     }
   }
-  return 0.5 * (a + b);
+  std::sort(knots.begin(), knots.end());
+  double best_t = 0.0, best = d2(0.0);
+  for (size_t j = 0; j + 1 < knots.size(); ++j) {
+    const double lo = knots[j], hi = knots[j + 1];
+    if (!(hi > lo)) continue;
+    const double mid = 0.5 * (lo + hi);
+    count_flop(8);
+    // On this piece d2(t) = A t^2 + 2 Bc t + const, from the coordinates outside the box.
+    double A = 0.0, Bc = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double e = P[i] + mid * D[i];
+      if (e > he[i]) {
+        A += D[i] * D[i];
+        Bc += D[i] * (P[i] - he[i]);
+        count_flop(5);
+      } else if (e < -he[i]) {
+        A += D[i] * D[i];
+        Bc += D[i] * (P[i] + he[i]);
+        count_flop(5);
+      }
+    }
+    count_flop(4);
+    const double t = A > 0.0 ? std::min(std::max(-Bc / A, lo), hi) : mid;
+    const double v = d2(t);
+    if (v < best) {
+      best = v;
+      best_t = t;
+    }
+  }
+  return best_t;
+}
+
+// Parameter of the segment point closest to the box centre (box frame),
+// clamped to [0, 1]; a value decision (zero derivative).
+template <class T> inline double seg_center_param(const V3<T>& Pl, const V3<T>& dl) {
+  count_flop(14);
+  const double dd = val(dl.x) * val(dl.x) + val(dl.y) * val(dl.y) + val(dl.z) * val(dl.z);
+  if (!(dd > 0.0)) return 0.0;
+  const double t = -(val(Pl.x) * val(dl.x) + val(Pl.y) * val(dl.y) + val(Pl.z) * val(dl.z)) / dd;
+  return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
 }
 
 // Capsule (segment P + t d, radius r, body ba) against a box (centre cb,
 // rotation Rb, half extents he, body bb).  READING: contact at the closest
 // segment point; outside the box the normal is the separation direction, the
 // contact point is midway between the capsule surface and the box point;
-// inside, the normal is the face of least penetration.
+// when the segment meets the box, at the segment point closest to the box
+// centre, with the normal of that point's face of least penetration.
 template <class T> inline void capsule_box(const V3<T>& P, const V3<T>& d, double r, int ba, const V3<T>& cb,
                                            const M3<T>& Rb, const double* he, int bb, double mu, double el,
                                            std::vector<Contact<T>>& out) {
@@ -480,13 +521,22 @@ template <class T> inline void capsule_box(const V3<T>& P, const V3<T>& d, doubl
   V3<T> nl, pl;
   T depth;
   const double eps = 1e-6;
+  note_branch(val(d2) > eps * eps ? 80 : 81);
   if (val(d2) > eps * eps) {
+    int pattern = 0;  // which box-frame coordinates were clamped to a face, and to which
+    for (int i = 0; i < 3; ++i) pattern = 3 * pattern + (val(e[i]) >= he[i] ? 1 : (val(e[i]) <= -he[i] ? 2 : 0));
+    note_branch(120 + pattern);
     T dist = sqrt(d2);
     nl = mk(dv[0] / dist, dv[1] / dist, dv[2] / dist);
     depth = T(r) - dist;
     V3<T> qv = mk(q[0], q[1], q[2]);
     pl = T(0.5) * ((el3 - T(r) * nl) + qv);
   } else {
+    t = seg_center_param(Pl, dl);
+    el3 = Pl + T(t) * dl;
+    e[0] = el3.x;
+    e[1] = el3.y;
+    e[2] = el3.z;
     int k = 0;
     double best = 1e300;
     for (int i = 0; i < 3; ++i) {
@@ -494,6 +544,7 @@ template <class T> inline void capsule_box(const V3<T>& P, const V3<T>& d, doubl
       if (pen < best) { best = pen; k = i; }
     }
     double sg = val(e[k]) >= 0.0 ? 1.0 : -1.0;
+    note_branch(50 + 2 * k + (sg > 0.0 ? 1 : 0));
     T pen = T(he[k]) - T(sg) * e[k];
     T z(0.0);
     nl = mk(k == 0 ? T(sg) : z, k == 1 ? T(sg) : z, k == 2 ? T(sg) : z);
@@ -604,9 +655,12 @@ template <class T> inline void respond(const System& s, const Contact<T>& ct, co
   if (b >= 0) kn = kn + eff_mass_term(s, b, fr[b], lb, ct.n);
   if (!(val(kn) > 0.0)) return;
   T un = dot(u, ct.n);
-  T target = vmax(T(s.baumgarte / h) * ct.depth, T(-ct.e) * un);
+  T t_pen = T(s.baumgarte / h) * ct.depth;
+  T t_rest = T(-ct.e) * un;
+  const bool rest_wins = !(val(t_pen) > val(t_rest));
+  T target = vmax(t_pen, t_rest);
   T jn = vmax((target - un) / kn, T(0.0));
-  note_branch(10 + (val(jn) > 0.0 ? 1 : 0) + (val(target) == val(T(-ct.e) * un) ? 2 : 0));
+  note_branch(10 + (val(jn) > 0.0 ? 1 : 0) + (rest_wins ? 2 : 0));
   V3<T> J = jn * ct.n;
   V3<T> ut = u - un * ct.n;
   T ut2 = dot(ut, ut);

@@ -36,7 +36,9 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(s) <= t for s in srcs):
             return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp,
+    # -ffp-contract=off: no fused multiply-adds, so the FP64 results (and every
+    # branch decision taken on them) are the same on x86_64 and aarch64.
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
            os.path.join(_HERE, "oracle_capi.cpp"), "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)

@@ -271,7 +271,7 @@ __device__ __forceinline__ void joint_hinge_bwd(const JP& bp, const Pub& pp, con
   const V3 yc = mulc(f.R, bp.ac + 3);
   const V3 cr = cross(P1, yc);
   const float sy = dot(cr, P0), cx = dot(P1, yc);
-  const float th = atan2f(sy, cx);
+  const float th = fast_atan2(sy, cx);
   float L = 0.f;
   int lim = 0;
   if (th < bp.lo[0]) {
@@ -363,9 +363,9 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
   const float m12 = dot(P[1], Cc[2]), m22 = dot(P[2], Cc[2]);
   const float sq = sqrtf(fmaf(m00, m00, m01 * m01));
   float th[3];
-  th[0] = atan2f(-m12, m22);
-  th[1] = atan2f(m02, sq);
-  th[2] = atan2f(-m01, m00);
+  th[0] = fast_atan2(-m12, m22);
+  th[1] = fast_atan2(m02, sq);
+  th[2] = fast_atan2(-m01, m00);
   float L[3];
   int lim[3];
 #pragma unroll
@@ -602,6 +602,8 @@ __device__ __forceinline__ void pair_bwd(const SysP& S, const BodyP* bodies, con
       pl = 0.5f * (fma3(-pr.ra, nl, e) + q);
     } else {
       inside = 1;
+      tbox = seg_center_param(Pl, dlv);
+      e = fma3(tbox, dlv, Pl);
       const float px = he[0] - fabsf(e.x), py = he[1] - fabsf(e.y), pz = he[2] - fabsf(e.z);
       kk = 0;
       pen = px;

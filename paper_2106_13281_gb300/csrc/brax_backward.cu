@@ -102,8 +102,7 @@ __device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, 
     for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
     for (int k = b; k < S.P; k += B) pair_forward(S, bodies, pairs[k], gm, k, lane);
   } else {
-    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
-    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    plane_points_regs(S, bp, pr, planes, np < 2 ? np : 2, s, f, acc);
     for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
   }
   group_sync(bar, nthr);
@@ -142,8 +141,7 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
     for (int k = b; k < S.P; k += B) pair_forward(S, bodies, pairs[k], gm, k, lane);
   } else {
-    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
-    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    plane_points_regs(S, bp, pr, planes, np < 2 ? np : 2, s, f, acc);
     for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
   }
   group_sync(bar, nthr);

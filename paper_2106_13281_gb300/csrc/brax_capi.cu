@@ -195,6 +195,9 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
         }
     REQUIRE(n == J, "joints: the joint graph has a cycle");
     S.n_order = n;
+    int np = 0;
+    for (int b = 0; b < B; ++b) bodies[b].tree_slot = bodies[b].n_children > 0 ? np++ : -1;
+    S.n_parents = np;
   }
   // actuators
   for (int k = 0; k < A; ++k) {

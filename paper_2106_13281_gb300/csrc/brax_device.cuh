@@ -61,6 +61,11 @@ __device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.
 __device__ __forceinline__ V3 cross(V3 a, V3 b) {
   return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
+// c + a x b with each component one multiply and two fused multiply-adds
+__device__ __forceinline__ V3 cross_add(V3 a, V3 b, V3 c) {
+  return V3{fmaf(a.y, b.z, fmaf(-a.z, b.y, c.x)), fmaf(a.z, b.x, fmaf(-a.x, b.z, c.y)),
+            fmaf(a.x, b.y, fmaf(-a.y, b.x, c.z))};
+}
 __device__ __forceinline__ V3 fma3(float s, V3 a, V3 b) {  // s*a + b
   return V3{fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)};
 }
@@ -82,19 +87,17 @@ __device__ __forceinline__ V3 mulc(const M3& R, const float* o) { return mul(R, 
 
 // Rotation matrix of a unit quaternion (w, x, y, z), body to world.
 __device__ __forceinline__ M3 qmat(float qw, float qx, float qy, float qz) {
-  const float xx = qx * qx, yy = qy * qy, zz = qz * qz;
-  const float xy = qx * qy, xz = qx * qz, yz = qy * qz;
-  const float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+  const float x2 = qx + qx, y2 = qy + qy, z2 = qz + qz;
   M3 R;
-  R.m[0] = 1.f - 2.f * (yy + zz);
-  R.m[1] = 2.f * (xy - wz);
-  R.m[2] = 2.f * (xz + wy);
-  R.m[3] = 2.f * (xy + wz);
-  R.m[4] = 1.f - 2.f * (xx + zz);
-  R.m[5] = 2.f * (yz - wx);
-  R.m[6] = 2.f * (xz - wy);
-  R.m[7] = 2.f * (yz + wx);
-  R.m[8] = 1.f - 2.f * (xx + yy);
+  R.m[0] = fmaf(-qy, y2, fmaf(-qz, z2, 1.f));
+  R.m[1] = fmaf(qx, y2, -qw * z2);
+  R.m[2] = fmaf(qx, z2, qw * y2);
+  R.m[3] = fmaf(qx, y2, qw * z2);
+  R.m[4] = fmaf(-qx, x2, fmaf(-qz, z2, 1.f));
+  R.m[5] = fmaf(qy, z2, -qw * x2);
+  R.m[6] = fmaf(qx, z2, -qw * y2);
+  R.m[7] = fmaf(qy, z2, qw * x2);
+  R.m[8] = fmaf(-qx, x2, fmaf(-qy, y2, 1.f));
   return R;
 }
 
@@ -127,9 +130,37 @@ __device__ __forceinline__ V3 mask3(uint32_t bits, V3 a) {
 
 __device__ __forceinline__ float clamp1(float a) { return fminf(fmaxf(a, -1.f), 1.f); }
 
+// Four-quadrant arctangent in (-pi, pi]: octant reduction to a = min/max in
+// [0, 1], atan(a) ~ a P(a^2) with a degree-7 polynomial fitted for this
+// library (csrc/gen_atan_poly.py; max error 1.3e-7 rad in FP32), then the
+// octant undone.  atan2(0, 0) = 0.
+__device__ __forceinline__ float fast_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float a = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+  const float s = a * a;
+  float p = -0.004037295f;
+  p = fmaf(p, s, 0.021790044f);
+  p = fmaf(p, s, -0.055787466f);
+  p = fmaf(p, s, 0.096311055f);
+  p = fmaf(p, s, -0.13903217f);
+  p = fmaf(p, s, 0.19945158f);
+  p = fmaf(p, s, -0.3332969f);
+  p = fmaf(p, s, 0.9999993f);
+  float r = a * p;
+  if (ay > ax) r = 1.5707963267948966f - r;
+  if (x < 0.f) r = 3.141592653589793f - r;
+  return copysignf(r, y);
+}
+
 // Named barrier for one group of warps (id 1..15; id 0 is __syncthreads).
 __device__ __forceinline__ void group_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Producer side of a named barrier: mark arrival without waiting.
+__device__ __forceinline__ void bar_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // ------------------------------------------------------------------ group shared memory

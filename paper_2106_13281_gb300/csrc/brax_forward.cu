@@ -22,9 +22,37 @@ template <bool kGeneral>
 __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodies, const PairP* pairs,
                                                const PlaneP* planes, const BodyP& bp, const HingeRegs& hr,
                                                const PointRegs* pr, int b, int B, int lane, GroupMem& gm, int bar,
-                                               int nthr, Body& s, const float* act) {
+                                               int nthr, bool tree, Body& s, const float* act) {
   kinematic(bp, S.h, s);
   const Frame f = make_frame(bp, s);
+  if (!kGeneral && tree) {
+    // Tree synchronisation: a child waits only for its parent's published
+    // state, a parent only for its own children's reactions.
+    const bool parent_of = bp.tree_slot >= 0;
+    const int my_n = 32 * (1 + bp.n_children);
+    if (parent_of) {
+      publish<false>(gm, b, lane, s, f);
+      bar_arrive(2 + 2 * bp.tree_slot, my_n);
+    }
+    // the own contacts need only the own state: do them while the parent publishes
+    Acc acc{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f), 0};
+    const int np = bp.n_points;
+    plane_points_regs(S, bp, pr, planes, np < 2 ? np : 2, s, f, acc);
+    for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+    const int counted = acc.n;
+    Wrench wr{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f)};
+    if (bp.flags & kHasParent) {
+      const BodyP& pb = bodies[bp.parent];
+      const int pid = 2 + 2 * pb.tree_slot, pn = 32 * (1 + pb.n_children);
+      group_sync(pid, pn);
+      const Pub pp = read_pub(gm, bp.parent, lane);
+      wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+      bar_arrive(pid + 1, pn);
+    }
+    if (parent_of) group_sync(3 + 2 * bp.tree_slot, my_n);
+    integrate<false>(S, bp, gm, lane, s, f, wr, acc);
+    return counted;
+  }
   if (bp.flags & kPublish) {
     if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
     else publish<false>(gm, b, lane, s, f);
@@ -41,8 +69,7 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
   if (kGeneral) {
     for (int i = 0; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
   } else {
-    if (np > 0) plane_point(S, bp, pr[0], planes[bp.pt[0].plane], s, f, acc);
-    if (np > 1) plane_point(S, bp, pr[1], planes[bp.pt[1].plane], s, f, acc);
+    plane_points_regs(S, bp, pr, planes, np < 2 ? np : 2, s, f, acc);
     for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
   }
   int counted = acc.n;
@@ -78,6 +105,8 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   GroupMem gm = group_mem(reinterpret_cast<float*>(smem) + g * group_floats(B, sg.P), B, sg.P);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
+  // tree barriers need the block to be exactly one group (their ids are per block)
+  const bool tree = !kGeneral && sg.groups == 1 && (int)blockDim.x == 32 * B && tree_barriers_fit(S.n_parents);
   if (b == 0) gm.cnt[lane] = 0;
   if (sg.ccount) group_sync(bar, nthr);
 
@@ -113,7 +142,8 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
       for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
     }
     for (int k = 0; k < nsub; ++k)
-      ccount += substep_forward<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
+      ccount += substep_forward<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, tree, s,
+                                          act);
     if (sg.torso && b == 0 && valid) {
       float* tp = sg.torso + ((int64_t)t * N + env) * 3;
       tp[0] = s.x.x;

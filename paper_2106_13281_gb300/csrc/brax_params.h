@@ -59,7 +59,7 @@ struct BodyP {
   float rest_rot[4];
   float frame_p[4], frame_c[4];  // joint frame quaternions (normalised)
   int32_t dof_offset;            // first joint-angle index of the parent joint
-  int32_t pad;
+  int32_t tree_slot;             // index among bodies with children (-1: none); names its two tree barriers
 };
 
 enum PairType : int32_t { kCapsuleCapsule = 0, kCapsuleBox = 1 };
@@ -92,7 +92,8 @@ struct SysP {
   int32_t pad3[3];
   int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
   int32_t n_order;
-  int32_t pad2[3];
+  int32_t n_parents;  // bodies with at least one child
+  int32_t pad2[2];
 };
 
 // Byte offsets inside the blob.
@@ -106,6 +107,12 @@ __host__ __device__ inline int blob_bytes(int B, int P, int n_planes) {
 
 // Shared memory of one group of 32 environments (floats), after the blob.
 constexpr int kPubFields = 24;  // x[3], R[9], v[3], w[3], Ii[6]
+// Tree barriers (one group per block): parent slot k owns named barrier
+// 2 + 2k (its published state, parent -> children) and 3 + 2k (its
+// children's reactions, children -> parent); each counts the parent's warp and
+// its children's warps.  Barrier 1 is the group barrier; 0 is __syncthreads.
+__host__ __device__ inline bool tree_barriers_fit(int n_parents) { return 3 + 2 * n_parents <= 16; }
+
 __host__ __device__ inline int group_floats(int B, int P) {
   return B * kPubFields * 32 + B * 6 * 32 + P * 8 * 32 + 32;
 }

@@ -209,11 +209,11 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
   const V3 rp = mulc(pp.R, bp.off_p);
   const V3 rc = mulc(f.R, bp.off_c);
   const V3 dpc = (pp.x + rp) - (s.x + rc);
-  const V3 up = pp.v + cross(pp.w, rp);
-  const V3 uc = s.v + cross(s.w, rc);
+  const V3 up = cross_add(pp.w, rp, pp.v);
+  const V3 uc = cross_add(s.w, rc, s.v);
   const V3 F = bp.k * dpc - bp.c * (uc - up);
   V3 tc = cross(rc, F);
-  V3 tp = -cross(rp, F);
+  V3 tp = cross(F, rp);
   const V3 P0 = mulc(pp.R, bp.ap + 0);
   const V3 P1 = mulc(pp.R, bp.ap + 3);
   const V3 wr = s.w - pp.w;
@@ -221,7 +221,7 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
   if (!kGeneral || bp.dof == 1) {
     const V3 Ac = mulc(f.R, bp.ac + 0);
     const V3 yc = mulc(f.R, bp.ac + 3);
-    const float th = atan2f(dot(cross(P1, yc), P0), dot(P1, yc));
+    const float th = fast_atan2(dot(cross(P1, yc), P0), dot(P1, yc));
     float L = 0.f;
     if (th < bp.lo[0]) L = bp.kl * (bp.lo[0] - th);
     else if (th > bp.hi[0]) L = bp.kl * (bp.hi[0] - th);
@@ -236,9 +236,9 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
     const float m00 = dot(P0, C0), m01 = dot(P0, C1), m02 = dot(P0, C2);
     const float m12 = dot(P1, C2), m22 = dot(P2, C2);
     float th[3];
-    th[0] = atan2f(-m12, m22);
-    th[1] = atan2f(m02, sqrtf(fmaf(m00, m00, m01 * m01)));
-    th[2] = atan2f(-m01, m00);
+    th[0] = fast_atan2(-m12, m22);
+    th[1] = fast_atan2(m02, sqrtf(fmaf(m00, m00, m01 * m01)));
+    th[2] = fast_atan2(-m01, m00);
     tj = -bp.ca * wr;
     const V3 Pk[3] = {P0, P1, P2};
 #pragma unroll
@@ -284,21 +284,16 @@ struct Eff {
   float inv_m;
 };
 
-// Plane contact of the own body: sphere (centre R o + x, radius r).
-template <class PT>
-__device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, const PT& pt, const PlaneP& pl,
-                                            const Body& s, const Frame& f, Acc& acc) {
-  const V3 ro = mulc(f.R, pt.o);
-  const V3 n = ld3(pl.n);
-  const float dist = dot((s.x + ro) - ld3(pl.p0), n);
-  const float depth = pt.r - dist;
-  if (!(depth > 0.f)) return;
-  const V3 l = fma3(-pt.r, n, ro);  // contact point e - r n, relative to the centre of mass
-  const V3 u = s.v + cross(s.w, l);
+// Velocity-level response of one contact of the own body against a static
+// plane: l is the contact point relative to the centre of mass, n the plane
+// normal, depth > 0 the penetration.
+__device__ __forceinline__ void point_response(const SysP& S, const BodyP& bp, V3 l, V3 n, float depth, float mu,
+                                               float e, const Body& s, const Frame& f, Acc& acc) {
+  const V3 u = cross_add(s.w, l, s.v);
   const float kn = eff_mass(bp.flags, bp.inv_mass, f.Ii, l, n);
   if (!(kn > 0.f)) return;
   const float un = dot(u, n);
-  const float target = fmaxf(S.beta_h * depth, -pt.e * un);
+  const float target = fmaxf(S.beta_h * depth, -e * un);
   const float jn = fmaxf(__fdividef(target - un, kn), 0.f);
   V3 J = jn * n;
   const V3 ut = fma3(-un, n, u);
@@ -308,7 +303,7 @@ __device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, cons
     const float utn = ut2 * rinv;
     const V3 t = rinv * ut;
     const float kt = eff_mass(bp.flags, bp.inv_mass, f.Ii, l, t);
-    const float jt = fminf(__fdividef(utn, kt), pt.mu * jn);
+    const float jt = fminf(__fdividef(utn, kt), mu * jn);
     J = fma3(-jt, t, J);
   }
   V3 dv = bp.inv_mass * J;
@@ -320,6 +315,55 @@ __device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, cons
   acc.dv = acc.dv + dv;
   acc.dw = acc.dw + dw;
   acc.n += 1;
+}
+
+// Plane contact of the own body: sphere (centre R o + x, radius r).
+template <class PT>
+__device__ __forceinline__ void plane_point(const SysP& S, const BodyP& bp, const PT& pt, const PlaneP& pl,
+                                            const Body& s, const Frame& f, Acc& acc) {
+  const V3 ro = mulc(f.R, pt.o);
+  const V3 n = ld3(pl.n);
+  const float dist = dot((s.x + ro) - ld3(pl.p0), n);
+  const float depth = pt.r - dist;
+  if (!(depth > 0.f)) return;
+  point_response(S, bp, fma3(-pt.r, n, ro), n, depth, pt.mu, pt.e, s, f, acc);
+}
+
+// Up to two register-resident contact points of the own body.  Both are
+// detected; then each lane handles its active points in order, so the warp
+// runs the response as many times as the largest per-lane active count
+// (a warp whose lanes touch the plane at different points runs it once).
+__device__ __forceinline__ void plane_points_regs(const SysP& S, const BodyP& bp, const PointRegs* pr,
+                                                  const PlaneP* planes, int np, const Body& s, const Frame& f,
+                                                  Acc& acc) {
+  if (np <= 0) return;
+  const PlaneP& pl0 = planes[bp.pt[0].plane];
+  const V3 n0 = ld3(pl0.n);
+  const V3 ro0 = mulc(f.R, pr[0].o);
+  const float dep0 = pr[0].r - dot((s.x + ro0) - ld3(pl0.p0), n0);
+  V3 n1 = n0, ro1 = ro0;
+  float dep1 = -1.f;
+  if (np > 1) {
+    const PlaneP& pl1 = planes[bp.pt[1].plane];
+    n1 = ld3(pl1.n);
+    ro1 = mulc(f.R, pr[1].o);
+    dep1 = pr[1].r - dot((s.x + ro1) - ld3(pl1.p0), n1);
+  }
+  const bool a0 = dep0 > 0.f, a1 = dep1 > 0.f;
+  const int cnt = (int)a0 + (int)a1;
+  const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+  for (int it = 0; it < maxc; ++it) {
+    if (it < cnt) {
+      const bool p1 = it > 0 || !a0;
+      const V3 n = p1 ? n1 : n0;
+      const V3 ro = p1 ? ro1 : ro0;
+      const float r = p1 ? pr[1].r : pr[0].r;
+      const float depth = p1 ? dep1 : dep0;
+      const float mu = p1 ? pr[1].mu : pr[0].mu;
+      const float e = p1 ? pr[1].e : pr[0].e;
+      point_response(S, bp, fma3(-r, n, ro), n, depth, mu, e, s, f, acc);
+    }
+  }
 }
 
 // Closest points of segments P1 + s d1 and P2 + t d2 (s, t in [0, 1]);
@@ -358,37 +402,59 @@ __device__ __forceinline__ void segment_closest(V3 P1, V3 d1, V3 P2, V3 d2, floa
   }
 }
 
-// Squared distance from a box-frame point to the box.
-__device__ __forceinline__ float box_d2(V3 e, const float* he) {
-  const float dx = e.x - fminf(fmaxf(e.x, -he[0]), he[0]);
-  const float dy = e.y - fminf(fmaxf(e.y, -he[1]), he[1]);
-  const float dz = e.z - fminf(fmaxf(e.z, -he[2]), he[2]);
-  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+// Parameter of the segment point closest to the box centre, clamped to
+// [0, 1]; used when the segment meets the box.  A value decision (no
+// derivative flows through it).
+__device__ __forceinline__ float seg_center_param(V3 Pl, V3 dl) {
+  const float dd = dot(dl, dl);
+  if (!(dd > 0.f)) return 0.f;
+  return fminf(fmaxf(-__fdividef(dot(Pl, dl), dd), 0.f), 1.f);
 }
 
-// Golden-section minimisation of the segment-box distance over the segment
-// parameter (24 iterations, one new evaluation each).
+// Half the derivative in t of the squared distance from the point e(t) of
+// the segment (direction dl) to the box: sum_i dl_i (e_i - clamp(e_i)).
+__device__ __forceinline__ float box_dist_slope(V3 e, V3 dl, const float* he) {
+  const float rx = e.x - fminf(fmaxf(e.x, -he[0]), he[0]);
+  const float ry = e.y - fminf(fmaxf(e.y, -he[1]), he[1]);
+  const float rz = e.z - fminf(fmaxf(e.z, -he[2]), he[2]);
+  return fmaf(dl.x, rx, fmaf(dl.y, ry, dl.z * rz));
+}
+
+// Exact minimiser over t in [0, 1] of the squared distance from Pl + t dl to
+// the box (box frame).  The squared distance is convex and C1 with a
+// piecewise-linear, non-decreasing slope whose kinks are the face-plane
+// crossings t = (+-he_i - Pl_i) / dl_i.  The root of the slope is bracketed
+// by the kinks (each kink inside the current bracket replaces the end whose
+// slope sign it shares) and, with no kink left inside, found by linear
+// interpolation.  A value decision (no derivative flows through it).
 __device__ __forceinline__ float seg_box_param(V3 Pl, V3 dl, const float* he) {
-  const float rho = 0.6180339887498949f;
-  float a = 0.f, b = 1.f;
-  float c = b - rho * (b - a), d = a + rho * (b - a);
-  float fc = box_d2(fma3(c, dl, Pl), he), fd = box_d2(fma3(d, dl, Pl), he);
-  for (int it = 0; it < 24; ++it) {
-    if (fc < fd) {
-      b = d;
-      d = c;
-      fd = fc;
-      c = b - rho * (b - a);
-      fc = box_d2(fma3(c, dl, Pl), he);
-    } else {
-      a = c;
-      c = d;
-      fc = fd;
-      d = a + rho * (b - a);
-      fd = box_d2(fma3(d, dl, Pl), he);
+  float gl = box_dist_slope(Pl, dl, he);
+  if (gl >= 0.f) return 0.f;
+  float gr = box_dist_slope(Pl + dl, dl, he);
+  if (gr <= 0.f) return 1.f;
+  float tl = 0.f, tr = 1.f;
+  const float P[3] = {Pl.x, Pl.y, Pl.z}, D[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (D[i] == 0.f) continue;
+    const float inv = 1.f / D[i];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const float t = ((side ? he[i] : -he[i]) - P[i]) * inv;
+      if (t > tl && t < tr) {
+        const float g = box_dist_slope(fma3(t, dl, Pl), dl, he);
+        if (g == 0.f) return t;
+        if (g < 0.f) {
+          tl = t;
+          gl = g;
+        } else {
+          tr = t;
+          gr = g;
+        }
+      }
     }
   }
-  return 0.5f * (a + b);
+  return fmaf(tr - tl, __fdividef(gl, gl - gr), tl);
 }
 
 // Detect one body-body pair; on contact compute the impulse on body a and
@@ -431,8 +497,8 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
     const V3 Pl = mulT(Rb, P1 - cb);
     const V3 dl = mulT(Rb, d1);
     const float* he = pr.b1;
-    const float t = seg_box_param(Pl, dl, he);
-    const V3 e = fma3(t, dl, Pl);
+    float t = seg_box_param(Pl, dl, he);
+    V3 e = fma3(t, dl, Pl);
     const V3 q = mk3(fminf(fmaxf(e.x, -he[0]), he[0]), fminf(fmaxf(e.y, -he[1]), he[1]),
                      fminf(fmaxf(e.z, -he[2]), he[2]));
     const V3 dv = e - q;
@@ -445,6 +511,8 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
       depth = pr.ra - dist;
       pl = 0.5f * (fma3(-pr.ra, nl, e) + q);
     } else {
+      t = seg_center_param(Pl, dl);
+      e = fma3(t, dl, Pl);
       const float px = he[0] - fabsf(e.x), py = he[1] - fabsf(e.y), pz = he[2] - fabsf(e.z);
       int kk = 0;
       float pen = px;

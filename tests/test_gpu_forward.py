@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as orc
 from paper_2106_13281_gb300 import scenes as S
+from parity_util import decided_envs
 
 pytestmark = pytest.mark.gpu
 
@@ -56,8 +57,16 @@ def test_default_qp_matches_oracle(brax, name):
 
 
 def settled_states(d, name, N, seed, drop, T=30):
-    """States after T oracle steps (contacts, limits and joints active)."""
+    """States after T oracle steps (contacts, limits and joints active).
+    Free bodies (the capsule-box scenes) start tilted with random velocities
+    and take one step only: once the capsule lies flat on a box face the
+    closest segment point, hence the contact point, is not unique."""
     st, _ = initial(d, N, seed, jitter=0.05, drop=drop)
+    if len(d["parent"]) == 0:
+        rng = np.random.default_rng(seed)
+        st[:, :, 7:10] += 0.3 * rng.normal(size=st[:, :, 7:10].shape)
+        st[:, :, 10:13] += 2.0 * rng.normal(size=st[:, :, 10:13].shape)
+        T = 1
     a = S.actions(d, N, T, seed).astype(np.float64)
     return f32(orc.rollout(d, st, a)).astype(np.float64)
 
@@ -74,9 +83,11 @@ def test_one_step_parity(brax, name, drop):
     out = sysm.rollout(cuda(st), cuda(a), contact_count=True)
     got = out["state_T"].cpu().numpy()
     assert np.isfinite(got).all()
-    dpos = np.abs(got[..., 0:3] - ref[..., 0:3]).max()
+    ok = decided_envs(d, st, a.astype(np.float64))
+    assert ok.mean() >= 0.9
+    dpos = np.abs(got[ok][..., 0:3] - ref[ok][..., 0:3]).max()
     assert dpos <= 1e-5, dpos
-    dq = np.abs(got[..., 3:7] - ref[..., 3:7]).max()
+    dq = np.abs(got[ok][..., 3:7] - ref[ok][..., 3:7]).max()
     assert dq <= 1e-4, dq
     cc = out["contact_count"].cpu().numpy()
     assert cc_ref.sum() > 0 or name == "pendulum"

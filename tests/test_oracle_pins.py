@@ -296,8 +296,8 @@ def test_segment_closest_brute_force():
 def test_capsule_box_brute_force():
     rng = np.random.default_rng(2)
     tgrid = np.linspace(0, 1, 20001)
-    n_hit = 0
-    for _ in range(60):
+    n_hit = n_inside = 0
+    for _ in range(120):
         he = rng.uniform(0.05, 0.3, size=3)
         c = rng.normal(size=3) * 0.2
         q = axis_angle(rng.normal(size=3), rng.uniform(0, 3))
@@ -311,33 +311,64 @@ def test_capsule_box_brute_force():
         dist = np.linalg.norm(res, axis=1)
         mind = dist.min()
         out = orc.capsule_box(P, Q, r, c, q, he)
+        step = np.linalg.norm(Q - P) * (tgrid[1] - tgrid[0])  # sampling step along the segment
+        pen = (he[None, :] - np.abs(loc)).min(axis=1)
+        if pen.max() > 1e-3:  # the segment clearly meets the box: point closest to the box centre
+            assert out is not None
+            depth, n, p = out
+            j = np.argmin(np.linalg.norm(loc, axis=1))
+            gaps = np.sort(he - np.abs(loc[j]))
+            assert abs(depth - (r + pen[j])) <= step + 1e-9
+            if gaps[1] - gaps[0] > 4 * step:  # a unique face of least penetration
+                k = np.argmin(he - np.abs(loc[j]))
+                nl = np.zeros(3)
+                nl[k] = np.sign(loc[j][k])
+                assert np.allclose(n, R @ nl, atol=1e-12)
+                p_ref = c + R @ (loc[j] + 0.5 * (pen[j] - r) * nl)
+                assert np.linalg.norm(p - p_ref) <= 2 * step + 1e-9
+            n_inside += 1
         if mind > 1e-6:
-            if r - mind > 1e-6:
+            if r - mind > 1e-9:
                 assert out is not None
                 depth, n, p = out
-                assert abs(depth - (r - mind)) < 1e-6
+                # the exact minimum lies at or below the sampled one, by at most one sampling step
+                assert -1e-12 <= depth - (r - mind) <= step + 1e-9
                 n_hit += 1
-            elif r - mind < -1e-6:
+            elif r - mind < -step - 1e-9:
                 assert out is None
-    assert n_hit > 5
+    assert n_hit > 5 and n_inside > 5
 
 
-def test_golden_section_parameter():
-    """The golden-section parameter minimises the convex segment-box distance."""
+def test_closest_parameter_minimises_distance():
+    """The segment parameter is the exact minimiser of the convex piecewise-
+    quadratic segment-box squared distance: never above the best of a fine
+    grid, and at the grid's minimiser where that minimiser is unique."""
     rng = np.random.default_rng(3)
     tgrid = np.linspace(0, 1, 100001)
-    for _ in range(30):
+    n_int = 0
+    for _ in range(60):
         he = rng.uniform(0.05, 0.3, size=3)
         Pl = rng.normal(size=3) * 0.5
         dl = rng.normal(size=3) * 0.5
         t = orc.seg_box_param(Pl, dl, he)
         f = lambda tt: np.sum((Pl + np.outer(tt, dl) - np.clip(Pl + np.outer(tt, dl), -he, he)) ** 2, axis=-1)
         fg = f(tgrid)
-        if fg.min() < 1e-14:  # the segment enters the box: any point of the zero set
-            assert f(np.array([t]))[0] < 1e-12
-        else:  # strictly convex: within the final golden-section bracket of the minimiser
-            rho24 = (0.5 * (5 ** 0.5 - 1)) ** 24
-            assert abs(t - tgrid[np.argmin(fg)]) <= rho24 + 2e-5
+        assert 0.0 <= t <= 1.0
+        assert f(np.array([t]))[0] <= fg.min() + 1e-15
+        if fg.min() > 1e-6:  # strictly convex near the minimiser: the parameter is unique
+            assert abs(t - tgrid[np.argmin(fg)]) <= 2e-5
+            n_int += 0.0 < t < 1.0
+    he = np.array([0.1, 0.1, 0.1])
+    # beyond the +x face, moving away from it: the start point
+    assert orc.seg_box_param(np.array([0.2, 0.0, 0.3]), np.array([0.3, 0.0, 0.0]), he) == 0.0
+    # e = (-0.5 + t, 0, 0.5 - 0.2 t): on t in [0.6, 1] the squared distance is
+    # (t - 0.6)^2 + (0.4 - 0.2 t)^2, stationary at t = 1.36 / 2.08 = 17/26
+    t = orc.seg_box_param(np.array([-0.5, 0.0, 0.5]), np.array([1.0, 0.0, -0.2]), he)
+    assert abs(t - 17.0 / 26.0) < 1e-14
+    # parallel to the top face, 0.2 above it: every t in [0.4, 0.6] is a minimiser
+    t = orc.seg_box_param(np.array([-0.5, 0.0, 0.3]), np.array([1.0, 0.0, 0.0]), he)
+    assert 0.4 - 1e-15 <= t <= 0.6 + 1e-15
+    assert n_int > 5
 
 
 def test_box_plane_depth_is_lowest_corner():
