@@ -39,11 +39,11 @@ __host__ __device__ inline int bwd_extra_floats(int B, int P) {
   return B * 6 * 32 + B * 18 * 32 + (P > 0 ? B * 6 * 32 + B * 18 * 32 : 0);
 }
 __host__ __device__ inline int bwd_fwd_floats(int B, int P, bool slots_in_smem) {
-  return B * kPubFields * 32 + B * 6 * 32 + (slots_in_smem ? P * 8 * 32 : 0) + 32;
+  return B * kPubFields * 32 + B * kReactFields * 32 + (slots_in_smem ? P * kSlotFields * 32 : 0) + 32;
 }
 __host__ __device__ inline int bwd_group_floats(int B, int P) { return bwd_fwd_floats(B, P, false) + bwd_extra_floats(B, P); }
 __host__ __device__ inline int64_t ws_group_floats(int B, int P, int K, int S) {
-  return (int64_t)(K + S) * 13 * B * 32 + (int64_t)P * 8 * 32;
+  return (int64_t)(K + S) * 13 * B * 32 + (int64_t)P * kSlotFields * 32;
 }
 
 struct BwdMem {
@@ -93,8 +93,8 @@ __device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, 
   Wrench wr{zero3(), zero3()};
   if (bp.flags & kHasParent) {
     const Pub pp = read_pub(gm, bp.parent, lane);
-    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
-    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.react4(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.react4(b, 0) + lane);
   }
   Acc acc{zero3(), zero3(), 0};
   const int np = bp.n_points;
@@ -132,8 +132,8 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   Pub pp;
   if (bp.flags & kHasParent) {
     pp = read_pub(gm, bp.parent, lane);
-    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
-    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.react4(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.react4(b, 0) + lane);
   }
   Acc acc{zero3(), zero3(), 0};
   const int np = bp.n_points;
@@ -149,12 +149,13 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   int n_pair = 0;
   if (kGeneral)
     for (int i = 0; i < bp.n_bpairs; ++i)
-      if (gm.slotf(bp.bpair[i] >> 1, 6)[lane] != 0.f) ++n_pair;
+      if (gm.slot4(bp.bpair[i] >> 1, 1)[lane].z != 0.f) ++n_pair;
   V3 Ft = wr.F, Tt = wr.tau;
-  for (int c = 0; c < bp.n_children; ++c) {
-    const float* r = gm.reactf(bp.children[c], 0) + lane;
-    Ft = Ft + mk3(r[0], r[32], r[64]);
-    Tt = Tt + mk3(r[96], r[128], r[160]);
+  {
+    Wrench sum{Ft, Tt};
+    for (int c = 0; c < bp.n_children; ++c) add_reaction(gm, bp.children[c], lane, sum);
+    Ft = sum.F;
+    Tt = sum.tau;
   }
   // ---- reverse P: potential and collision integrators
   const int n = acc.n + n_pair;
@@ -234,7 +235,7 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   if (kGeneral) {
     for (int k = b; k < S.P; k += B) {
       const PairP& prk = pairs[k];
-      if (gm.slotf(k, 6)[lane] == 0.f) continue;
+      if (gm.slot4(k, 1)[lane].z == 0.f) continue;
       GSide GA, GB;
       zero(GA);
       zero(GB);
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
   GroupMem gm = group_mem(gbase, B, 0);
   const int K = L.K, T = L.T, nsub = S.substeps;
   float* ws = sg.ws + group * ws_group_floats(B, P, K, nsub);
-  if (kGeneral) gm.slot = ws + (int64_t)(K + nsub) * 13 * B * 32;  // pair impulses live in the workspace
+  if (kGeneral) gm.slot = reinterpret_cast<float4*>(ws + (int64_t)(K + nsub) * 13 * B * 32);  // pair impulses live in the workspace
   BwdMem bm;
   bm.gwr = gbase + bwd_fwd_floats(B, P, false);
   bm.gpub = bm.gwr + B * 6 * 32;

@@ -46,7 +46,7 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
       const int pid = 2 + 2 * pb.tree_slot, pn = 32 * (1 + pb.n_children);
       group_sync(pid, pn);
       const Pub pp = read_pub(gm, bp.parent, lane);
-      wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+      wr = joint_forward<false>(hr, pp, s, f, act, gm.react4(b, 0) + lane);
       bar_arrive(pid + 1, pn);
     }
     if (parent_of) group_sync(3 + 2 * bp.tree_slot, my_n);
@@ -61,8 +61,8 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
   Wrench wr{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f)};
   if (bp.flags & kHasParent) {
     const Pub pp = read_pub(gm, bp.parent, lane);
-    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.reactf(b, 0) + lane);
-    else wr = joint_forward<false>(hr, pp, s, f, act, gm.reactf(b, 0) + lane);
+    if (kGeneral) wr = joint_forward<true>(bp, pp, s, f, act, gm.react4(b, 0) + lane);
+    else wr = joint_forward<false>(hr, pp, s, f, act, gm.react4(b, 0) + lane);
   }
   Acc acc{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f), 0};
   const int np = bp.n_points;

@@ -106,7 +106,9 @@ __host__ __device__ inline int blob_bytes(int B, int P, int n_planes) {
 }
 
 // Shared memory of one group of 32 environments (floats), after the blob.
-constexpr int kPubFields = 24;  // x[3], R[9], v[3], w[3], Ii[6]
+constexpr int kPubFields = 24;    // x[3], R[9], v[3], w[3], Ii[6]: six float4 per lane
+constexpr int kReactFields = 8;   // F[3], tau[3], 2 pad: two float4 per lane
+constexpr int kSlotFields = 8;    // J[3], p[3], active flag, pad: two float4 per lane
 // Tree barriers (one group per block): parent slot k owns named barrier
 // 2 + 2k (its published state, parent -> children) and 3 + 2k (its
 // children's reactions, children -> parent); each counts the parent's warp and
@@ -114,7 +116,7 @@ constexpr int kPubFields = 24;  // x[3], R[9], v[3], w[3], Ii[6]
 __host__ __device__ inline bool tree_barriers_fit(int n_parents) { return 3 + 2 * n_parents <= 16; }
 
 __host__ __device__ inline int group_floats(int B, int P) {
-  return B * kPubFields * 32 + B * 6 * 32 + P * 8 * 32 + 32;
+  return B * kPubFields * 32 + B * kReactFields * 32 + P * kSlotFields * 32 + 32;
 }
 
 }  // namespace brax

@@ -99,21 +99,16 @@ __device__ __forceinline__ Frame make_frame(const BodyP& bp, const Body& s) {
 
 template <bool kIi>
 __device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Body& s, const Frame& f) {
-  float* p = gm.pubf(b, 0) + lane;
-  p[0 * 32] = s.x.x;
-  p[1 * 32] = s.x.y;
-  p[2 * 32] = s.x.z;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) p[(3 + i) * 32] = f.R.m[i];
-  p[12 * 32] = s.v.x;
-  p[13 * 32] = s.v.y;
-  p[14 * 32] = s.v.z;
-  p[15 * 32] = s.w.x;
-  p[16 * 32] = s.w.y;
-  p[17 * 32] = s.w.z;
+  float4* p = gm.pub4(b, 0) + lane;
+  p[0] = make_float4(s.x.x, s.x.y, s.x.z, f.R.m[0]);
+  p[32] = make_float4(f.R.m[1], f.R.m[2], f.R.m[3], f.R.m[4]);
+  p[64] = make_float4(f.R.m[5], f.R.m[6], f.R.m[7], f.R.m[8]);
+  p[96] = make_float4(s.v.x, s.v.y, s.v.z, s.w.x);
   if (kIi) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) p[(18 + i) * 32] = f.Ii.a[i];
+    p[128] = make_float4(s.w.y, s.w.z, f.Ii.a[0], f.Ii.a[1]);
+    p[160] = make_float4(f.Ii.a[2], f.Ii.a[3], f.Ii.a[4], f.Ii.a[5]);
+  } else {
+    st2(p + 128, s.w.y, s.w.z);
   }
 }
 
@@ -123,20 +118,35 @@ struct Pub {
   V3 v, w;
 };
 __device__ __forceinline__ Pub read_pub(GroupMem& gm, int b, int lane) {
-  const float* p = gm.pubf(b, 0) + lane;
+  const float4* p = gm.pub4(b, 0) + lane;
+  const float4 c0 = p[0], c1 = p[32], c2 = p[64], c3 = p[96];
+  const float2 c4 = ld2(p + 128);
   Pub o;
-  o.x = mk3(p[0], p[32], p[64]);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) o.R.m[i] = p[(3 + i) * 32];
-  o.v = mk3(p[12 * 32], p[13 * 32], p[14 * 32]);
-  o.w = mk3(p[15 * 32], p[16 * 32], p[17 * 32]);
+  o.x = mk3(c0.x, c0.y, c0.z);
+  o.R.m[0] = c0.w;
+  o.R.m[1] = c1.x;
+  o.R.m[2] = c1.y;
+  o.R.m[3] = c1.z;
+  o.R.m[4] = c1.w;
+  o.R.m[5] = c2.x;
+  o.R.m[6] = c2.y;
+  o.R.m[7] = c2.z;
+  o.R.m[8] = c2.w;
+  o.v = mk3(c3.x, c3.y, c3.z);
+  o.w = mk3(c3.w, c4.x, c4.y);
   return o;
 }
 __device__ __forceinline__ S6 read_pub_Ii(GroupMem& gm, int b, int lane) {
-  const float* p = gm.pubf(b, 18) + lane;
+  const float4* p = gm.pub4(b, 4) + lane;
+  const float2 a = ld2hi(p);
+  const float4 c = p[32];
   S6 s;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) s.a[i] = p[i * 32];
+  s.a[0] = a.x;
+  s.a[1] = a.y;
+  s.a[2] = c.x;
+  s.a[3] = c.y;
+  s.a[4] = c.z;
+  s.a[5] = c.w;
   return s;
 }
 
@@ -205,7 +215,7 @@ __device__ __forceinline__ PointRegs point_regs(const PointP& p) {
 // the child's wrench; writes the parent's to the react buffer.
 template <bool kGeneral, class JP>
 __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, const Body& s, const Frame& f,
-                                                const float* act, float* react_out /* reactf(b,0)+lane */) {
+                                                const float* act, float4* react_out /* react4(b,0)+lane */) {
   const V3 rp = mulc(pp.R, bp.off_p);
   const V3 rc = mulc(f.R, bp.off_c);
   const V3 dpc = (pp.x + rp) - (s.x + rc);
@@ -252,12 +262,8 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
   }
   tc = tc + tj;
   tp = tp - tj;
-  react_out[0 * 32] = -F.x;
-  react_out[1 * 32] = -F.y;
-  react_out[2 * 32] = -F.z;
-  react_out[3 * 32] = tp.x;
-  react_out[4 * 32] = tp.y;
-  react_out[5 * 32] = tp.z;
+  react_out[0] = make_float4(-F.x, -F.y, -F.z, tp.x);
+  st2(react_out + 32, tp.y, tp.z);
   return Wrench{F, tc};
 }
 
@@ -530,10 +536,10 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
       hit = true;
     }
   }
-  float* sl = gm.slotf(k, 0) + lane;
+  float4* sl = gm.slot4(k, 0) + lane;
   if (!hit) {
-#pragma unroll
-    for (int i = 0; i < 7; ++i) sl[i * 32] = 0.f;
+    sl[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    sl[32] = make_float4(0.f, 0.f, 0.f, 0.f);
     return 0;
   }
   const BodyP& ba = bodies[pr.ba];
@@ -544,8 +550,8 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
   const V3 u = (A.v + cross(A.w, la)) - (Bq.v + cross(Bq.w, lb));
   const float kn = eff_mass(ba.flags, ba.inv_mass, Ia, la, n) + eff_mass(bb.flags, bb.inv_mass, Ib, lb, n);
   if (!(kn > 0.f)) {
-#pragma unroll
-    for (int i = 0; i < 7; ++i) sl[i * 32] = 0.f;
+    sl[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    sl[32] = make_float4(0.f, 0.f, 0.f, 0.f);
     return 0;
   }
   const float un = dot(u, n);
@@ -562,34 +568,36 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
     const float jt = fminf(__fdividef(utn, kt), pr.mu * jn);
     J = fma3(-jt, t, J);
   }
-  sl[0 * 32] = J.x;
-  sl[1 * 32] = J.y;
-  sl[2 * 32] = J.z;
-  sl[3 * 32] = p.x;
-  sl[4 * 32] = p.y;
-  sl[5 * 32] = p.z;
-  sl[6 * 32] = 1.f;
+  sl[0] = make_float4(J.x, J.y, J.z, p.x);
+  sl[32] = make_float4(p.y, p.z, 1.f, 0.f);
   return 1;
 }
 
 // ------------------------------------------------------------------ phase P
+// Add a child's joint reaction (force, torque on this body) to wr.
+__device__ __forceinline__ void add_reaction(GroupMem& gm, int child, int lane, Wrench& wr) {
+  const float4* r = gm.react4(child, 0) + lane;
+  const float4 a = r[0];
+  const float2 b = ld2(r + 32);
+  wr.F = wr.F + mk3(a.x, a.y, a.z);
+  wr.tau = wr.tau + mk3(a.w, b.x, b.y);
+}
+
 // Potential integrator: v += h (F/m + g), w += h Ii tau; collision
 // integrator: the mean (or sum) of the contact velocity changes.
 template <bool kGeneral>
 __device__ __forceinline__ void integrate(const SysP& S, const BodyP& bp, GroupMem& gm, int lane, Body& s,
                                           const Frame& f, Wrench wr, Acc acc) {
-  for (int c = 0; c < bp.n_children; ++c) {
-    const float* r = gm.reactf(bp.children[c], 0) + lane;
-    wr.F = wr.F + mk3(r[0], r[32], r[64]);
-    wr.tau = wr.tau + mk3(r[96], r[128], r[160]);
-  }
+  for (int c = 0; c < bp.n_children; ++c) add_reaction(gm, bp.children[c], lane, wr);
   for (int i = 0; kGeneral && i < bp.n_bpairs; ++i) {
     const int code = bp.bpair[i];
-    const float* sl = gm.slotf(code >> 1, 0) + lane;
-    if (sl[6 * 32] != 0.f) {
+    const float4* sl = gm.slot4(code >> 1, 0) + lane;
+    const float4 c1 = sl[32];
+    if (c1.z != 0.f) {
+      const float4 c0 = sl[0];
       const float sg = (code & 1) ? -1.f : 1.f;
-      const V3 J = sg * mk3(sl[0], sl[32], sl[64]);
-      const V3 l = mk3(sl[96], sl[128], sl[160]) - s.x;
+      const V3 J = sg * mk3(c0.x, c0.y, c0.z);
+      const V3 l = mk3(c0.w, c1.x, c1.y) - s.x;
       V3 dv = bp.inv_mass * J;
       V3 dw = mul(f.Ii, cross(l, J));
       if (bp.flags & kAnyFrozen) {
