@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         L.brax_rollout_backward_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P]
         if hasattr(L, "brax_system_set_launch"):
             L.brax_system_set_launch.argtypes = [P, i32, i32]
+        if hasattr(L, "brax_system_set_pair_launch"):
+            L.brax_system_set_pair_launch.argtypes = [P, i32, i32, i32]
         _lib = L
         return L
 

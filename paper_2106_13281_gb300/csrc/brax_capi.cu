@@ -364,7 +364,65 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   S.eps = d.contact_eps;
   for (int i = 0; i < 3; ++i) S.g[i] = d.gravity[i];
 
-  std::vector<unsigned char> blob(blob_bytes(B, Pb, S.n_planes), 0);
+  // Two environments per thread need hinge joints only and at most two
+  // plane-contact points per body.
+  bool paired = !S.general;
+  for (int b = 0; b < B; ++b) paired = paired && bodies[b].n_points <= 2;
+  const int base_bytes = blob_bytes(B, Pb, S.n_planes);
+  S.paired = paired ? 1 : 0;
+  S.pair_off = paired ? base_bytes : 0;
+  std::vector<unsigned char> blob(base_bytes + (paired ? blob_pair_bytes(B) : 0), 0);
+  if (paired) {
+    auto f2 = [](float v) { return make_float2(v, v); };
+    SysP2 S2;
+    std::memset(&S2, 0, sizeof(S2));
+    S2.h = f2(S.h);
+    S2.mhh = f2(-0.5f * S.h);
+    S2.hh = f2(0.5f * S.h);
+    S2.beta_h = f2(S.beta_h);
+    S2.eps2 = f2(S.eps * S.eps);
+    for (int i = 0; i < 3; ++i) S2.g[i] = f2(S.g[i]);
+    S2.one = f2(1.f);
+    S2.mone = f2(-1.f);
+    std::memcpy(blob.data() + base_bytes, &S2, sizeof(S2));
+    for (int b = 0; b < B; ++b) {
+      const BodyP& bp = bodies[b];
+      BodyP2 q;
+      std::memset(&q, 0, sizeof(q));
+      for (int i = 0; i < 3; ++i) {
+        q.off_p[i] = f2(bp.off_p[i]);
+        q.off_c[i] = f2(bp.off_c[i]);
+        q.inv_I[i] = f2(bp.inv_I[i]);
+      }
+      for (int i = 0; i < 6; ++i) {
+        q.ap[i] = f2(bp.ap[i]);
+        q.ac[i] = f2(bp.ac[i]);
+      }
+      q.k = f2(bp.k);
+      q.mc = f2(-bp.c);
+      q.ka = f2(bp.ka);
+      q.mca = f2(-bp.ca);
+      q.kl = f2(bp.kl);
+      q.lo = f2(bp.lo[0]);
+      q.hi = f2(bp.hi[0]);
+      q.gear = f2(bp.gear[0]);
+      q.inv_mass = f2(bp.inv_mass);
+      for (int k = 0; k < bp.n_points; ++k) {
+        const PointP& pt = bp.pt[k];
+        const PlaneP& pl = planes[pt.plane];
+        for (int i = 0; i < 3; ++i) {
+          q.pt[k].o[i] = f2(pt.o[i]);
+          q.pt[k].n[i] = f2(pl.n[i]);
+          q.pt[k].p0[i] = f2(pl.p0[i]);
+        }
+        q.pt[k].r = f2(pt.r);
+        q.pt[k].mr = f2(-pt.r);
+        q.pt[k].mu = f2(pt.mu);
+        q.pt[k].me = f2(-pt.e);
+      }
+      std::memcpy(blob.data() + base_bytes + sizeof(SysP2) + b * sizeof(BodyP2), &q, sizeof(q));
+    }
+  }
   std::memcpy(blob.data(), &S, sizeof(SysP));
   std::memcpy(blob.data() + blob_bodies_off(), bodies.data(), sizeof(BodyP) * B);
   if (Pb) std::memcpy(blob.data() + blob_pairs_off(B), pairs.data(), sizeof(PairP) * Pb);
@@ -494,6 +552,10 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   }
   s->groups = 1;
   s->variant = pick_variant(32 * s->B);
+  s->paired = S->paired != 0;
+  s->pair_groups = 1;
+  s->pair_variant = 0;
+  s->pair_mode = (s->paired && 32 * s->B <= pair_variant_max_threads(0)) ? 1 : 0;
   *out = s;
   return BRAX_OK;
 }
@@ -527,6 +589,23 @@ int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant) {
   return BRAX_OK;
 }
 
+// Two-environments-per-thread launch override (mode 0: off, 1: on; groups of
+// 64 environments per block; launch-bounds variant); used by the autotuner.
+int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant) {
+  if (!s || mode < 0 || mode > 1 || groups < 1 || groups > 15 || variant < 0 || variant > 3)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_pair_launch: bad arguments");
+  if (mode == 1 && !s->paired)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_pair_launch: the system has no paired kernel");
+  if (mode == 1 && 32 * s->B * groups > pair_variant_max_threads(variant))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_pair_launch: block too large for the variant");
+  s->pair_mode = mode;
+  if (mode == 1) {
+    s->pair_groups = groups;
+    s->pair_variant = variant;
+  }
+  return BRAX_OK;
+}
+
 int brax_default_qp(const brax_system* s, int64_t n_envs, const float* root_pos, const float* root_rot,
                     const float* joint_angles, float* state_out, void* stream) {
   if (!s || !state_out || n_envs < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_default_qp: bad arguments");
@@ -548,6 +627,29 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   L.n_segs = 1;
   L.T = T;
   L.K = K < 1 ? 1 : K;
+  // Two environments per thread for plain forward rollouts.  A rollout that
+  // writes checkpoints feeds the reverse pass, which recomputes the substeps
+  // between checkpoints with the one-environment arithmetic: it runs that
+  // kernel too, so gradients do not depend on the checkpoint interval.
+  if (s->pair_mode == 1 && !checkpoints) {
+    Seg sg = make_seg(s, s->pair_groups, n_envs);
+    const int64_t per_cta = 64LL * s->pair_groups;
+    const int64_t grid = (n_envs + per_cta - 1) / per_cta;
+    if (grid > 0x7fffffff) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: too many environments");
+    sg.cta_begin = 0;
+    sg.cta_end = (int32_t)grid;
+    sg.state0 = state0;
+    sg.actions = actions;
+    sg.state_T = state_T;
+    sg.ckpt = checkpoints;
+    sg.torso = torso_traj;
+    sg.ccount = contact_count;
+    L.seg[0] = sg;
+    const size_t smem = s->pair_groups * pair_group_bytes(s->B);
+    cudaError_t e = launch_rollout_pair(L, (int)grid, 32 * s->B * s->pair_groups, smem, s->pair_variant,
+                                        as_stream(stream));
+    return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
+  }
   Seg sg = make_seg(s, s->groups, n_envs);
   const int64_t per_cta = 32LL * s->groups;
   const int64_t grid = (n_envs + per_cta - 1) / per_cta;

@@ -10,6 +10,7 @@
 // two named barriers (see brax_physics.cuh).  Every warp is uniform in its
 // body role, so the only divergence is data-dependent (limits, contacts).
 #include "brax_kernels.h"
+#include "brax_pair.cuh"
 #include "brax_physics.cuh"
 
 namespace brax {
@@ -161,6 +162,145 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   }
 }
 
+// ------------------------------------------------------------------ two environments per thread
+namespace p2 {
+// Load environment A's and B's body into the pair state (a padding half
+// steps the body's rest pose).
+__device__ __forceinline__ void load_pair(const float* pa, const float* pb, const BodyP& bp, Body& s) {
+  auto ld = [&](int i) {
+    const float r = i < 3 ? bp.rest_pos[i] : (i < 7 ? bp.rest_rot[i - 3] : 0.f);
+    return make_float2(pa ? pa[i] : r, pb ? pb[i] : r);
+  };
+  s.x = V{ld(0), ld(1), ld(2)};
+  s.qw = ld(3);
+  s.qx = ld(4);
+  s.qy = ld(5);
+  s.qz = ld(6);
+  s.v = V{ld(7), ld(8), ld(9)};
+  s.w = V{ld(10), ld(11), ld(12)};
+}
+// Store one half (0: A, 1: B) of the pair state.
+__device__ __forceinline__ void store_half(float* p, const Body& s, int half) {
+  auto h = [half](f2 v) { return half ? v.y : v.x; };
+  p[0] = h(s.x.x);
+  p[1] = h(s.x.y);
+  p[2] = h(s.x.z);
+  p[3] = h(s.qw);
+  p[4] = h(s.qx);
+  p[5] = h(s.qy);
+  p[6] = h(s.qz);
+  p[7] = h(s.v.x);
+  p[8] = h(s.v.y);
+  p[9] = h(s.v.z);
+  p[10] = h(s.w.x);
+  p[11] = h(s.w.y);
+  p[12] = h(s.w.z);
+}
+__device__ __forceinline__ bool finite_pair(const Body& s) {
+  const f2 t = add(add(add(s.x.x, s.x.y), add(s.x.z, s.qw)),
+                   add(add(add(s.qx, s.qy), add(s.qz, s.v.x)), add(add(s.v.y, s.v.z), add(s.w.x, add(s.w.y, s.w.z)))));
+  return fabsf(t.x) < INFINITY && fabsf(t.y) < INFINITY;
+}
+}  // namespace p2
+
+// Persistent rollout of a hinge-only system, two environments per thread
+// (brax_pair.cuh).  One launch segment; a block holds G groups of 64
+// environments.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_constant__ Launch L) {
+  using namespace p2;
+  const Seg& sg = L.seg[0];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned char* blob = c_pool + sg.pool_off;
+  const SysP& S = *reinterpret_cast<const SysP*>(blob);
+  const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
+  const SysP2& S2 = *reinterpret_cast<const SysP2*>(blob + S.pair_off);
+  const BodyP2* bodies2 = reinterpret_cast<const BodyP2*>(blob + S.pair_off + sizeof(SysP2));
+  const int B = sg.B;
+  const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
+  const int lane = threadIdx.x & 31;
+  const int g = warp / B, b = warp - g * B;
+  if (g >= sg.groups) return;  // spare warps take no part in the group barriers
+  const int64_t N = sg.n_envs;
+  const int64_t ea = ((int64_t)blockIdx.x * sg.groups + g) * 64 + lane, eb = ea + 32;
+  const bool va = ea < N, vb = eb < N;
+  GroupMem2 gm = group_mem2(reinterpret_cast<float*>(smem) + g * group_floats2(B), B);
+  const int bar = 1 + g, nthr = 32 * B;
+  const BodyP& bp = bodies[b];
+  const BodyP2& q = bodies2[b];
+  if (b == 0) {
+    gm.cnt[lane] = 0;
+    gm.cnt[32 + lane] = 0;
+  }
+  if (sg.ccount) group_sync(bar, nthr);
+  p2::Body s;
+  load_pair(va ? sg.state0 + (ea * B + b) * 13 : nullptr, vb ? sg.state0 + (eb * B + b) * 13 : nullptr, bp, s);
+  const int T = L.T, K = L.K, A = sg.A;
+  const int nsub = S.substeps;
+  const bool has_parent = (bp.flags & kHasParent) != 0, publishes = (bp.flags & kPublish) != 0;
+  const int act_idx = bp.act[0];
+  const int np = bp.n_points;
+  const bool average = S.average != 0;
+  int cca = 0, ccb = 0;
+  bool bad = false;
+  for (int t = 0; t < T; ++t) {
+    if (sg.ckpt && (t % K) == 0) {
+      float* c = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
+      if (va) store_half(c + (ea * B + b) * 13, s, 0);
+      if (vb) store_half(c + (eb * B + b) * 13, s, 1);
+    }
+    f2 act = zero2();
+    if (has_parent && act_idx >= 0) {
+      const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
+      act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
+    }
+    for (int k = 0; k < nsub; ++k) {
+      kinematic(S2, bp.flags, s);
+      p2::Frame f;
+      f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
+      if (publishes) publish(gm, b, lane, s, f);
+      group_sync(bar, nthr);
+      if (has_parent) {
+        const p2::Pub pp = read_pub(gm, bp.parent, lane);
+        joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
+      }
+      p2::Acc acc{vzero(), vzero(), 0, 0};
+      f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
+      plane_points(S2, q, bp.flags, np, s, f, acc);
+      cca += acc.na;
+      ccb += acc.nb;
+      group_sync(bar, nthr);
+      integrate(S2, average, bp, q, gm, b, lane, s, f, acc);
+    }
+    if (sg.torso && b == 0) {
+      float* tp = sg.torso + (int64_t)t * N * 3;
+      if (va) {
+        tp[ea * 3 + 0] = s.x.x.x;
+        tp[ea * 3 + 1] = s.x.y.x;
+        tp[ea * 3 + 2] = s.x.z.x;
+      }
+      if (vb) {
+        tp[eb * 3 + 0] = s.x.x.y;
+        tp[eb * 3 + 1] = s.x.y.y;
+        tp[eb * 3 + 2] = s.x.z.y;
+      }
+    }
+    bad |= !finite_pair(s);
+  }
+  if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
+  if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
+  if (bad && (va || vb)) atomicOr(sg.status, 1);
+  if (sg.ccount) {
+    atomicAdd(&gm.cnt[lane], cca);
+    atomicAdd(&gm.cnt[32 + lane], ccb);
+    group_sync(bar, nthr);
+    if (b == 0) {
+      if (va) sg.ccount[ea] = gm.cnt[lane];
+      if (vb) sg.ccount[eb] = gm.cnt[32 + lane];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ default_qp
 __device__ __forceinline__ void qmul4(const float* a, const float* b, float* o) {
   const float r0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
@@ -261,6 +401,30 @@ cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, 
     default: return launch_rollout_t<1024, 1, false>(L, grid, threads, smem, st);
   }
 }
+
+template <int MAXT, int MINB>
+static cudaError_t launch_pair_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
+  auto k = rollout_pair_kernel<MAXT, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+// Two-environments-per-thread variants: 0: (288, 2)  1: (576, 1)  2: (1024, 1)  3: (288, 3)
+cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st) {
+  switch (variant) {
+    case 0: return launch_pair_t<288, 2>(L, grid, threads, smem, st);
+    case 1: return launch_pair_t<576, 1>(L, grid, threads, smem, st);
+    case 3: return launch_pair_t<288, 3>(L, grid, threads, smem, st);
+    default: return launch_pair_t<1024, 1>(L, grid, threads, smem, st);
+  }
+}
+int pair_variant_max_threads(int variant) {
+  static const int t[4] = {288, 576, 1024, 288};
+  return (variant >= 0 && variant < 4) ? t[variant] : 0;
+}
+size_t pair_group_bytes(int B) { return (size_t)p2::group_floats2(B) * sizeof(float); }
 
 int rollout_variant_max_threads(int variant) {
   static const int t[4] = {384, 576, 1024, 288};

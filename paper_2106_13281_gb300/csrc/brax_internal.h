@@ -16,6 +16,12 @@ struct brax_system {
   int32_t* d_status = nullptr;
   int groups = 1;   // groups of 32 environments per thread block
   int variant = 0;  // launch-bounds variant of the rollout kernel
+  // Two environments per thread (hinge-only systems with at most two plane
+  // points per body): used for brax_rollout / brax_step when pair_mode is 1.
+  bool paired = false;
+  int pair_mode = 0;
+  int pair_groups = 1;   // groups of 64 environments per thread block
+  int pair_variant = 0;  // launch-bounds variant of the paired kernel
 };
 
 

@@ -14,6 +14,10 @@ cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, 
 cudaError_t upload_pool_forward(int off, const void* data, size_t bytes);
 cudaError_t upload_pool_backward(int off, const void* data, size_t bytes);
 int rollout_variant_max_threads(int variant);
+// Two environments per thread (systems whose blob carries the paired section).
+cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+int pair_variant_max_threads(int variant);
+size_t pair_group_bytes(int B);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);
 size_t backward_smem_bytes(int B, int P, int groups);

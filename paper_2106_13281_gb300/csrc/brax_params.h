@@ -9,6 +9,7 @@
 // pairs it takes part in.
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>
 
 #include "../../include/brax.h"
 
@@ -88,12 +89,39 @@ struct SysP {
   float h, beta_h, eps, pad0;  // beta_h = baumgarte / h
   float g[3];
   float pad1;
-  int32_t general;  // 1: the system has a 3-DOF joint or a body-body pair
-  int32_t pad3[3];
+  int32_t general;   // 1: the system has a 3-DOF joint or a body-body pair
+  int32_t paired;    // 1: the blob carries SysP2/BodyP2 (two environments per thread)
+  int32_t pair_off;  // byte offset of SysP2 in the blob
+  int32_t pad3;
   int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
   int32_t n_order;
   int32_t n_parents;  // bodies with at least one child
   int32_t pad2[2];
+};
+
+// Two environments per thread (systems with hinge joints only and at most
+// two plane-contact points per body).  The floating-point parameters a warp
+// uses every substep, each duplicated into a (value, value) pair so that it
+// is a ready operand of the packed FP32 instructions; appended to the blob.
+// Negated copies (m*) let the kernel write a - b*c as one fused multiply-add:
+// the packed instructions take no negated operand.
+struct SysP2 {
+  float2 h, mhh, beta_h, eps2;  // h, -h/2, baumgarte/h, contact_eps^2
+  float2 g[3];
+  float2 one, mone;             // (1, 1), (-1, -1)
+  float2 hh;                    // h/2
+};
+struct PointP2 {
+  float2 o[3];          // sphere centre, body frame
+  float2 r, mr, mu, me; // radius, -radius, friction, -elasticity
+  float2 n[3], p0[3];   // its plane's normal and a point on it
+};
+struct BodyP2 {
+  float2 off_p[3], off_c[3];
+  float2 ap[6], ac[6];  // joint frame x and y axes in the parent's / this body's frame
+  float2 k, mc, ka, mca, kl, lo, hi, gear;  // mc = -c, mca = -ca
+  float2 inv_mass, inv_I[3];
+  PointP2 pt[2];
 };
 
 // Byte offsets inside the blob.
@@ -104,6 +132,8 @@ __host__ __device__ inline int blob_bytes(int B, int P, int n_planes) {
   int b = blob_planes_off(B, P) + n_planes * (int)sizeof(PlaneP);
   return (b + 15) & ~15;
 }
+// The paired section (SysP2, BodyP2[B]) starts at blob_bytes(B, P, n_planes).
+__host__ __device__ inline int blob_pair_bytes(int B) { return (int)sizeof(SysP2) + B * (int)sizeof(BodyP2); }
 
 // Shared memory of one group of 32 environments (floats), after the blob.
 constexpr int kPubFields = 24;    // x[3], R[9], v[3], w[3], Ii[6]: six float4 per lane

@@ -47,7 +47,15 @@ class BraxSystem:
         return self._h
 
     def set_launch(self, groups: int, variant: int):
+        """Launch of the one-environment-per-thread kernel (groups of 32
+        environments per block, launch-bounds variant 0..3)."""
         check(self._L.brax_system_set_launch(self._h, groups, variant))
+
+    def set_pair_launch(self, mode: int, groups: int = 1, variant: int = 0):
+        """Two-environments-per-thread kernel of hinge-only systems: mode 1
+        uses it for rollout/step (groups of 64 environments per block), mode 0
+        falls back to the one-environment kernel."""
+        check(self._L.brax_system_set_pair_launch(self._h, mode, groups, variant))
 
     # ---------------------------------------------------------------- forward
     def default_qp(self, n_envs, root_pos=None, root_rot=None, angles=None):

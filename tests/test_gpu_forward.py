@@ -155,10 +155,12 @@ def test_checkpoints_and_torso(brax):
     ck, tor = out["checkpoints"], out["torso"]
     assert ck.shape[0] == math.ceil(T / K)
     assert torch.equal(ck[0], cuda(st))
+    # a checkpointing rollout runs the one-environment kernel (the arithmetic
+    # the reverse pass recomputes with): compare with rollouts of that kernel
     for k in range(1, ck.shape[0]):
-        part = sysm.rollout(cuda(st), a[:k * K].contiguous())["state_T"]
+        part = sysm.rollout(cuda(st), a[:k * K].contiguous(), K=k * K, checkpoints=True)["state_T"]
         assert torch.equal(ck[k], part)
-    part = sysm.rollout(cuda(st), a[:7].contiguous())["state_T"]
+    part = sysm.rollout(cuda(st), a[:7].contiguous(), K=7, checkpoints=True)["state_T"]
     assert torch.equal(tor[6], part[:, 0, 0:3])
     assert torch.equal(tor[T - 1], out["state_T"][:, 0, 0:3])
 
@@ -194,3 +196,37 @@ def test_nonfinite_state_reported(brax):
     st[17, 3, 8] = 0.0
     sysm.rollout(cuda(st), cuda(a))
     sysm.sync_status()
+
+
+@pytest.mark.parametrize("name,drop", [("quadruped", 0.38), ("pendulum", 0.0)])
+def test_pair_kernel_matches_single_env_kernel(brax, name, drop):
+    """Hinge-only systems run two environments per thread by default; the
+    one-environment kernel computes the same step (rounding aside): one-step
+    states within 1e-5, identical contact counts, checkpoints and torso
+    output laid out alike, ragged tails (N = 37: one pair of half-empty
+    lanes) included."""
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    for N in (37, 100):
+        st, _ = initial(d, N, 11, drop=drop)
+        a = cuda(S.actions(d, N, 1, 12))
+        outs = []
+        for mode in (1, 0):
+            sysm.set_pair_launch(mode, 1, 0)
+            outs.append(sysm.rollout(cuda(st), a, torso=True, contact_count=True))
+            sysm.sync_status()
+        p, q = outs
+        dx = (p["state_T"] - q["state_T"]).abs()
+        assert dx[..., :7].max().item() < 1e-5  # positions and orientations
+        assert dx.max().item() < 1e-4           # velocities (m/s, rad/s)
+        assert (p["torso"] - q["torso"]).abs().max().item() < 1e-5
+        assert torch.equal(p["contact_count"], q["contact_count"])
+    sysm.set_pair_launch(1, 1, 0)
+
+
+def test_pair_launch_rejected_for_general_systems(brax):
+    from paper_2106_13281_gb300.binding import BraxError
+    sysm = brax(S.biped())
+    with pytest.raises(BraxError):
+        sysm.set_pair_launch(1, 1, 0)
+    sysm.set_pair_launch(0)
