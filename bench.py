@@ -42,7 +42,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--envs", type=int, default=65536)
     p.add_argument("--horizon", type=int, default=1000, help="steps per rollout")
-    p.add_argument("--checkpoint-every", type=int, default=10, help="K of the fwd+bwd figure")
+    p.add_argument("--checkpoint-every", type=int, default=0,
+                   help="K of the fwd+bwd figure (0: picked by the autotuner)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -157,6 +159,19 @@ def run_ours(args):
     actions = f32(S.actions(d, N, T, seed))
     state_T = torch.empty_like(state0)
     stream = torch.cuda.current_stream()
+    # launch configuration and checkpoint interval: picked by timing the
+    # workload itself (brax_autotune), before any timed region
+    tuning = {"autotuned": not args.no_autotune}
+    K = args.checkpoint_every if args.checkpoint_every > 0 else 10
+    if not args.no_autotune:
+        r = sysm.autotune(state0, actions)
+        tuning.update(fwd_kernel="two_envs_per_thread" if r["fwd_kernel"] else "one_env_per_thread",
+                      fwd_groups=r["fwd_groups"], fwd_variant=r["fwd_variant"], fwd_candidates=r["n_candidates"])
+        if args.checkpoint_every <= 0:
+            nt = min(N, 16384)  # the reverse candidates are timed on a slice of the workload
+            rr_ = sysm.autotune(state0[:nt].contiguous(), actions[:, :nt].contiguous(), reverse=True, forward=False)
+            K = rr_["K"]
+            tuning.update(K=K, bwd_variant=rr_["bwd_variant"], reverse_sample_envs=nt)
 
     def step():
         sysm.rollout(state0, actions, state_T=state_T)
@@ -212,7 +227,6 @@ def run_ours(args):
     d2h = h_out.numel() * 4
 
     # forward + reverse pass of the same workload (checkpoints every K steps)
-    K = args.checkpoint_every
     gT = torch.zeros_like(state0)
     gT[:, 0, 0] = -1.0  # d/dstate_T of -(torso x displacement)
     ckpt = torch.empty((math.ceil(T / K), N, sysm.B, 13), device="cuda", dtype=torch.float32)
@@ -275,6 +289,7 @@ def run_ours(args):
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                      "flops_per_env_step": flops_per_envstep, "kernel_ms": kern_ms},
         "clocks": clk.summary(),
+        "tuning": tuning,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(d, sysm, seed)

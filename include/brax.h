@@ -216,6 +216,36 @@ int brax_batch_rollout_backward(const brax_batch* batch, int32_t T, int32_t K, c
  * a non-finite state.  Also reports a pending CUDA error as BRAX_ERR_CUDA. */
 int brax_sync_status(const brax_system* sys, void* stream);
 
+/* ---------------------------------------------------------------- autotuner
+ * Picks, by timing on the caller's own sample, the launch configuration of
+ * the forward rollout (one or two environments per thread, environment
+ * groups per thread block, launch-bounds variant) and, with
+ * BRAX_TUNE_REVERSE, the checkpoint interval K and the reverse kernel's
+ * launch-bounds variant.  The chosen configuration is applied to `sys` and
+ * returned in `out` (K is advice: the caller passes it to brax_rollout and
+ * brax_rollout_backward).
+ *   state0 [n_envs, B, 13], actions [T, n_envs, A]: device arrays of the
+ *     workload (the forward is timed on min(T, 10) steps of it, the reverse
+ *     on min(T, max(2 K, 20)) steps per candidate K);
+ *   mem_budget: bytes the reverse candidates may hold (checkpoints +
+ *     workspace); 0 = half of the free device memory.
+ * Unlike the compute calls this one allocates temporary device memory and
+ * synchronizes `stream`.  Returns BRAX_OK, or the first error of a call it
+ * could not recover from. */
+enum { BRAX_TUNE_FORWARD = 1, BRAX_TUNE_REVERSE = 2 };
+typedef struct {
+  int32_t fwd_kernel;   /* 0: one environment per thread, 1: two */
+  int32_t fwd_groups;   /* environment groups per thread block (32 or 64 environments each) */
+  int32_t fwd_variant;  /* launch-bounds variant */
+  float fwd_ms;         /* time of the forward sample with that configuration */
+  int32_t K;            /* checkpoint interval (BRAX_TUNE_REVERSE), else 0 */
+  int32_t bwd_variant;  /* reverse kernel launch-bounds variant, else -1 */
+  float fwd_bwd_ms_per_step; /* forward with checkpoints + reverse, per step of the sample */
+  int32_t n_candidates; /* configurations timed */
+} brax_tune_result;
+int brax_autotune(brax_system* sys, int64_t n_envs, int32_t T, const float* state0, const float* actions,
+                  int32_t flags, size_t mem_budget, void* stream, brax_tune_result* out);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* brax_last_error(void);
 

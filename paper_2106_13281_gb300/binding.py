@@ -23,13 +23,22 @@ STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_DESCRIPTOR", 3: "CUDA", 4:
 EXPORTS = ["brax_system_create", "brax_system_destroy", "brax_system_info", "brax_default_qp", "brax_step",
            "brax_rollout", "brax_workspace_size", "brax_rollout_backward", "brax_batch_create",
            "brax_batch_destroy", "brax_batch_offsets", "brax_batch_rollout", "brax_batch_workspace_size",
-           "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error", "brax_rollout_backward_noalloc"]
+           "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error", "brax_rollout_backward_noalloc",
+           "brax_autotune"]
+
+BRAX_TUNE_FORWARD, BRAX_TUNE_REVERSE = 1, 2
 
 
 class BraxError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"brax error {code} ({STATUS.get(code, '?')}): {msg}")
         self.code = code
+
+
+class brax_tune_result(C.Structure):
+    _fields_ = [("fwd_kernel", C.c_int32), ("fwd_groups", C.c_int32), ("fwd_variant", C.c_int32),
+                ("fwd_ms", C.c_float), ("K", C.c_int32), ("bwd_variant", C.c_int32),
+                ("fwd_bwd_ms_per_step", C.c_float), ("n_candidates", C.c_int32)]
 
 
 class brax_desc(C.Structure):
@@ -93,11 +102,15 @@ def load_library(path: str = LIB_PATH):
         L.brax_batch_workspace_size.argtypes = [P, i32, i32, C.POINTER(C.c_size_t)]
         L.brax_batch_rollout_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, P, P, C.c_size_t, P]
         L.brax_sync_status.argtypes = [P, P]
+        L.brax_autotune.argtypes = [P, i64, i32, P, P, i32, C.c_size_t, P, C.POINTER(brax_tune_result)]
         L.brax_rollout_backward_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P]
         if hasattr(L, "brax_system_set_launch"):
             L.brax_system_set_launch.argtypes = [P, i32, i32]
         if hasattr(L, "brax_system_set_pair_launch"):
             L.brax_system_set_pair_launch.argtypes = [P, i32, i32, i32]
+            L.brax_system_get_launch.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
+            L.brax_system_get_pair_launch.argtypes = [P, C.POINTER(i32)]
+            L.brax_system_set_backward_launch.argtypes = [P, i32]
         _lib = L
         return L
 

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbrax_gb300.so")
-SOURCES = ["brax_capi.cu", "brax_forward.cu", "brax_backward.cu"]
+SOURCES = ["brax_capi.cu", "brax_forward.cu", "brax_backward.cu", "brax_tune.cu"]
 HEADERS = ["brax_params.h", "brax_device.cuh", "brax_physics.cuh", "brax_kernels.h", "brax_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: single-instruction approximate reciprocal square root and division

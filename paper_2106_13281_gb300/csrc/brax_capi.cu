@@ -445,32 +445,47 @@ namespace {
 size_t group_bytes(const brax_system* s) { return (size_t)group_floats(s->B, s->P) * sizeof(float); }
 
 // First-fit allocator of the constant parameter pool, one per device.
+// Systems with byte-identical blobs share one range (reference counted), so
+// many handles of one scene cost the pool once.
 struct PoolRange {
-  int device, off, bytes;
+  int device, off, bytes, refs;
+  std::vector<unsigned char> content;
 };
 std::vector<PoolRange> g_pool;
 std::mutex g_pool_mu;
 
-int pool_alloc(int device, int bytes) {
+// Returns the offset of `blob` in the device's pool (uploading it to the
+// constant pools of the kernel translation units when it is new), -1 when
+// the pool is full, or -2 - cudaError when the upload failed.
+int pool_acquire(int device, const std::vector<unsigned char>& blob) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
-  std::vector<PoolRange> used;
+  for (auto& r : g_pool)
+    if (r.device == device && r.content == blob) {
+      ++r.refs;
+      return r.off;
+    }
+  const int bytes = (int)blob.size();
+  std::vector<const PoolRange*> used;
   for (const auto& r : g_pool)
-    if (r.device == device) used.push_back(r);
-  std::sort(used.begin(), used.end(), [](const PoolRange& a, const PoolRange& b) { return a.off < b.off; });
+    if (r.device == device) used.push_back(&r);
+  std::sort(used.begin(), used.end(), [](const PoolRange* a, const PoolRange* b) { return a->off < b->off; });
   int off = 0;
-  for (const auto& r : used) {
-    if (r.off - off >= bytes) break;
-    off = std::max(off, r.off + r.bytes);
+  for (const auto* r : used) {
+    if (r->off - off >= bytes) break;
+    off = std::max(off, r->off + r->bytes);
   }
   if (off + bytes > kPoolBytes) return -1;
-  g_pool.push_back(PoolRange{device, off, bytes});
+  cudaError_t e = upload_pool_forward(off, blob.data(), blob.size());
+  if (e == cudaSuccess) e = upload_pool_backward(off, blob.data(), blob.size());
+  if (e != cudaSuccess) return -2 - (int)e;
+  g_pool.push_back(PoolRange{device, off, bytes, 1, blob});
   return off;
 }
-void pool_free(int device, int off) {
+void pool_release(int device, int off) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (size_t i = 0; i < g_pool.size(); ++i)
     if (g_pool[i].device == device && g_pool[i].off == off) {
-      g_pool.erase(g_pool.begin() + i);
+      if (--g_pool[i].refs == 0) g_pool.erase(g_pool.begin() + i);
       return;
     }
 }
@@ -533,20 +548,20 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) {
-    s->pool_off = pool_alloc(s->device, (int)s->blob.size());
-    if (s->pool_off < 0) {
+    const int off = pool_acquire(s->device, s->blob);
+    if (off == -1) {
       cudaFree(s->d_blob);
       cudaFree(s->d_status);
       delete s;
       return fail(BRAX_ERR_OUT_OF_MEMORY, "brax_system_create: the constant parameter pool (60 KB per device) is full");
     }
-    e = upload_pool_forward(s->pool_off, s->blob.data(), s->blob.size());
-    if (e == cudaSuccess) e = upload_pool_backward(s->pool_off, s->blob.data(), s->blob.size());
+    if (off < -1) e = (cudaError_t)(-2 - off);
+    else s->pool_off = off;
   }
   if (e != cudaSuccess) {
     cudaFree(s->d_blob);
     if (s->d_status) cudaFree(s->d_status);
-    if (s->pool_off >= 0) pool_free(s->device, s->pool_off);
+    if (s->pool_off >= 0) pool_release(s->device, s->pool_off);
     delete s;
     return cuda_fail(e, "brax_system_create");
   }
@@ -562,7 +577,7 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
 
 void brax_system_destroy(brax_system* s) {
   if (!s) return;
-  if (s->pool_off >= 0) pool_free(s->device, s->pool_off);
+  if (s->pool_off >= 0) pool_release(s->device, s->pool_off);
   cudaFree(s->d_blob);
   cudaFree(s->d_status);
   delete s;
@@ -603,6 +618,28 @@ int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, in
     s->pair_groups = groups;
     s->pair_variant = variant;
   }
+  return BRAX_OK;
+}
+
+// Current launch configuration (for the autotuner's cache): the
+// one-environment kernel's groups and variant; the paired mode (-1: the
+// system has no paired kernel, else 0/1); the reverse kernel's variant.
+int brax_system_get_launch(const brax_system* s, int32_t* groups, int32_t* variant) {
+  if (!s || !groups || !variant) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_get_launch: null argument");
+  *groups = s->groups;
+  *variant = s->variant;
+  return BRAX_OK;
+}
+int brax_system_get_pair_launch(const brax_system* s, int32_t* mode) {
+  if (!s || !mode) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_get_pair_launch: null argument");
+  *mode = s->paired ? s->pair_mode : -1;
+  return BRAX_OK;
+}
+int brax_system_set_backward_launch(brax_system* s, int32_t variant) {
+  if (!s || variant < -1 || variant > 3) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_backward_launch: bad arguments");
+  if (variant >= 0 && 32 * s->B > rollout_variant_max_threads(variant))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_backward_launch: block too large for the variant");
+  s->bwd_variant = variant;
   return BRAX_OK;
 }
 
@@ -868,7 +905,8 @@ extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32
   sg.ws = reinterpret_cast<float*>(workspace);
   L.seg[0] = sg;
   const int threads = 32 * s->B;
-  const int variant = pick_variant(threads);
+  const int variant =
+      (s->bwd_variant >= 0 && threads <= rollout_variant_max_threads(s->bwd_variant)) ? s->bwd_variant : pick_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: system too large for one block");
   const size_t smem = backward_smem_bytes(s->B, s->P, 1);
   cudaError_t e = launch_rollout_backward(L, (int)grid, threads, smem, variant, s->general, st);

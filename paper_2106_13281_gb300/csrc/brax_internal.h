@@ -22,7 +22,11 @@ struct brax_system {
   int pair_mode = 0;
   int pair_groups = 1;   // groups of 64 environments per thread block
   int pair_variant = 0;  // launch-bounds variant of the paired kernel
+  int bwd_variant = -1;  // launch-bounds variant of the reverse kernel (-1: smallest that fits)
 };
+
+extern "C" int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant);
+extern "C" int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant);
 
 
 namespace brax {

@@ -4,11 +4,16 @@ libbrax_gb300.so."""
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
+import json
 import math
+import os
 
+import numpy as np
 import torch
 
-from .binding import _ptr, _stream, check, load_library, marshal_desc
+from .binding import (BRAX_TUNE_FORWARD, BRAX_TUNE_REVERSE, _ptr, _stream, brax_tune_result, check, load_library,
+                      marshal_desc)
 
 
 def _f32(t, shape=None, name="tensor"):
@@ -56,6 +61,67 @@ class BraxSystem:
         uses it for rollout/step (groups of 64 environments per block), mode 0
         falls back to the one-environment kernel."""
         check(self._L.brax_system_set_pair_launch(self._h, mode, groups, variant))
+
+    # ---------------------------------------------------------------- autotuner
+    def _desc_digest(self) -> str:
+        h = hashlib.sha1()
+        for k in sorted(self.desc):
+            h.update(k.encode())
+            h.update(np.ascontiguousarray(np.asarray(self.desc[k])).tobytes() if not isinstance(self.desc[k], str)
+                     else self.desc[k].encode())
+        return h.hexdigest()
+
+    def autotune(self, state0, actions, reverse: bool = False, mem_budget: int = 0, cache: str | None = None,
+                 forward: bool = True):
+        """Time the workload sample (state0 [N,B,13], actions [T,N,A]) under
+        every launch configuration and keep the fastest (brax_autotune); with
+        reverse=True also pick the checkpoint interval K.  Results are cached
+        in the JSON file `cache` (key: system, device, N, T, what), and a
+        cache hit applies the stored configuration without timing.  Returns a
+        dict with the chosen configuration (K for the reverse pass)."""
+        N, T = state0.shape[0], actions.shape[0]
+        _f32(state0, (N, self.B, 13), "state0")
+        _f32(actions, (T, N, self.A), "actions")
+        flags = (BRAX_TUNE_FORWARD if forward else 0) | (BRAX_TUNE_REVERSE if reverse else 0)
+        if not flags:
+            raise ValueError("autotune: nothing to tune")
+        key = f"{self._desc_digest()}|{torch.cuda.get_device_name()}|{N}|{T}|{flags}"
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        if key in table:
+            r = table[key]
+            if forward:
+                self.set_launch(r["scalar_groups"], r["scalar_variant"])
+                if r["fwd_kernel"] == 1:
+                    self.set_pair_launch(1, r["fwd_groups"], r["fwd_variant"])
+                elif self.paired:
+                    self.set_pair_launch(0)
+            if r.get("bwd_variant", -1) >= 0:
+                self._L.brax_system_set_backward_launch(self._h, r["bwd_variant"])
+            return dict(r, cached=True)
+        out = brax_tune_result()
+        check(self._L.brax_autotune(self._h, N, T, _ptr(state0), _ptr(actions), flags, mem_budget, _stream(),
+                                    C.byref(out)))
+        g, v = C.c_int32(), C.c_int32()
+        check(self._L.brax_system_get_launch(self._h, C.byref(g), C.byref(v)))
+        r = {k: getattr(out, k) for k, _ in brax_tune_result._fields_}
+        r.update(scalar_groups=g.value, scalar_variant=v.value)
+        if cache:
+            table[key] = r
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1)
+            os.replace(tmp, cache)
+        return dict(r, cached=False)
+
+    @property
+    def paired(self) -> bool:
+        """True when the system has the two-environments-per-thread kernel."""
+        m = C.c_int32()
+        check(self._L.brax_system_get_pair_launch(self._h, C.byref(m)))
+        return m.value >= 0
 
     # ---------------------------------------------------------------- forward
     def default_qp(self, n_envs, root_pos=None, root_rot=None, angles=None):
