@@ -46,6 +46,10 @@ def parse():
                    help="K of the fwd+bwd figure (0: picked by the autotuner)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="quadruped", choices=["quadruped", "biped", "adjoint", "hetero"],
+                   help="quadruped: the headline line; the others time the remaining configurations "
+                        "(biped forward 16384 x 1000; quadruped adjoint 4096 x 100 and x 1000; heterogeneous "
+                        "batch fwd+bwd 65536 x 200) and print one informational line each")
     return p.parse_args()
 
 
@@ -358,10 +362,127 @@ def run_reference(args):
     }), flush=True)
 
 
+def _timed(fn, warmup, steps):
+    """Mean ms of fn over `steps` runs after `warmup` runs (CUDA events on the
+    current stream, synchronised on both sides)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_workload(args):
+    """The other configurations of the method, one JSON line each (not the
+    headline): biped forward, quadruped adjoint, heterogeneous batch."""
+    import numpy as np
+    import torch
+
+    from paper_2106_13281_gb300 import scenes as S
+    from paper_2106_13281_gb300.system import BraxBatch, BraxSystem
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    steps = max(1, min(args.steps, 3))
+
+    def setup(name, N, T, seed, drop=0.0):
+        d = S.SCENES[name]()
+        sysm = BraxSystem(d)
+        rp, rr, ang = S.initial_conditions(d, N, seed, height_jitter=0.05)
+        rp[:, 2] -= drop
+        return d, sysm, sysm.default_qp(N, f32(rp), f32(rr), f32(ang)), f32(S.actions(d, N, T, seed))
+
+    def roof(flops_per_envstep, envsteps, ms):
+        t = flops_per_envstep * envsteps / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": t, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": t / FP32_PEAK_TFLOPS, "flops_per_env_step": flops_per_envstep}
+
+    lines = []
+    if args.workload == "biped":
+        N, T = 16384, 1000
+        d, sysm, st, a = setup("biped", N, T, 2)
+        r = sysm.autotune(st, a)
+        out = torch.empty_like(st)
+        ms = _timed(lambda: sysm.rollout(st, a, state_T=out), args.warmup, steps)
+        sysm.sync_status()
+        lines.append({"metric": "env-steps/s fwd, 17-body biped (self-collision) @16k envs", "value": N * T / ms * 1e3,
+                      "unit": "env-steps/s", "ms_per_step": ms, "steps": steps,
+                      "config": {"workload": "biped-17body forward rollout, 16384 envs x 1000 steps x 10 substeps"},
+                      "roofline": roof(alg_flops("biped")["flops_per_env_step"], N * T, ms),
+                      "tuning": {k: r[k] for k in ("fwd_kernel", "fwd_groups", "fwd_variant")}})
+    elif args.workload == "adjoint":
+        for T in (100, 1000):
+            N = 4096
+            d, sysm, st, a = setup("quadruped", N, T, 3, drop=0.0)
+            r = sysm.autotune(st, a, reverse=True)
+            K = r["K"]
+            gT = torch.zeros_like(st)
+            gT[:, 0, 0] = -1.0
+            ws = torch.empty((sysm.workspace_size(N, T, K),), device="cuda", dtype=torch.uint8)
+            out = torch.empty_like(st)
+
+            def fb2():
+                o = sysm.rollout(st, a, K=K, checkpoints=True, state_T=out)
+                sysm.rollout_backward(st, a, o["checkpoints"], gT, None, K=K, workspace=ws)
+
+            ms = _timed(fb2, args.warmup, steps)
+            sysm.sync_status()
+            lines.append({"metric": "env-steps/s fwd+bwd, 9-body quadruped adjoint @4096 envs",
+                          "value": N * T / ms * 1e3, "unit": "env-steps/s", "ms_per_step": ms, "steps": steps,
+                          "config": {"workload": f"quadruped adjoint, 4096 envs x {T} steps, loss -torso x "
+                                                 "displacement (+ action penalty, differentiated by torch)",
+                                     "checkpoint_every": K},
+                          "tuning": {k: r[k] for k in ("K", "bwd_variant", "fwd_bwd_ms_per_step")}})
+            del ws
+    else:  # heterogeneous batch, forward + reverse in one launch each
+        names, ns, T = ["pendulum", "quadruped", "biped", "arm_box"], [32768, 16384, 8192, 8192], 200
+        descs = [S.SCENES[n]() for n in names]
+        systems = [BraxSystem(dd) for dd in descs]
+        sts, acs, gts = [], [], []
+        for i, (dd, sy, n) in enumerate(zip(descs, systems, ns)):
+            rp, rr, ang = S.initial_conditions(dd, n, 4 + i, height_jitter=0.05)
+            st = sy.default_qp(n, f32(rp), f32(rr), f32(ang))
+            sts.append(st.reshape(-1))
+            acs.append(f32(S.actions(dd, n, T, 4 + i)).reshape(-1))
+            g = torch.zeros_like(st)
+            g[:, -1 if names[i] == "arm_box" else (len(dd["parent"]) if names[i] == "pendulum" else 0), 0] = -1.0
+            gts.append(g.reshape(-1))
+        batch = BraxBatch(systems, ns)
+        st, a, gT = torch.cat(sts), torch.cat(acs), torch.cat(gts)
+        K = 10
+        ws = torch.empty((batch.workspace_size(T, K),), device="cuda", dtype=torch.uint8)
+
+        def fwd():
+            return batch.rollout(st, a, T, K=K, checkpoints=True)
+
+        def fb():
+            o = fwd()
+            batch.rollout_backward(st, a, o["checkpoints"], gT, T, K=K, workspace=ws)
+
+        ms_f = _timed(fwd, args.warmup, steps)
+        ms = _timed(fb, args.warmup, steps)
+        fl = sum(alg_flops(n)["flops_per_env_step"] * k for n, k in zip(names, ns)) / sum(ns)
+        lines.append({"metric": "env-steps/s fwd+bwd, heterogeneous batch (one launch each way)",
+                      "value": sum(ns) * T / ms * 1e3, "unit": "env-steps/s", "ms_per_step": ms, "steps": steps,
+                      "fwd_only": {"value": sum(ns) * T / ms_f * 1e3, "ms_per_step": ms_f,
+                                   "roofline": roof(fl, sum(ns) * T, ms_f)},
+                      "config": {"workload": "32768 pendulum + 16384 quadruped + 8192 biped + 8192 arm+box, "
+                                             "200 steps, checkpoints every 10", "checkpoint_every": K}})
+    for ln in lines:
+        ln.update({"n_gpus": 1, "warmup": args.warmup, "dtype": "f32", "data": "synthetic", "higher_is_better": True})
+        print(json.dumps(ln), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "quadruped":
+        run_workload(args)
     else:
         run_ours(args)
 
