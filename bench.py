@@ -53,6 +53,32 @@ def parse():
     return p.parse_args()
 
 
+def kernel_sources_digest():
+    """sha256 over the CUDA sources (csrc/*.cu, *.cuh, *.h, sorted by name)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2106_13281_gb300", "csrc")
+    h = hashlib.sha256()
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            h.update(n.encode())
+            with open(os.path.join(d, n), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch of the dominant kernel from one ncu capture
+    (data/traffic.json), or None when the kernel sources changed since."""
+    p = os.path.join(ROOT, "paper_2106_13281_gb300", "data", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f).get(key)
+    if not rec or rec.get("sources_sha256") != kernel_sources_digest():
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def alg_flops(scene="quadruped"):
     with open(os.path.join(ROOT, "paper_2106_13281_gb300", "data", "alg_flops.json")) as f:
         return json.load(f)[scene]
@@ -263,6 +289,8 @@ def run_ours(args):
     fwd_bwd_value = aggregate_rate(world, N, T, fb_steps, fb_ms)
     del ws, ckpt
 
+    # state read and written once, actions read once (the per-launch algorithmic bytes)
+    algorithmic_bytes = 2 * state0.numel() * 4 + actions.numel() * 4
     fl = alg_flops("quadruped")
     flops_per_envstep = fl["flops_per_env_step"]
     achieved_tflops = flops_per_envstep * envsteps / (kern_ms / 1e3) / 1e12
@@ -289,7 +317,9 @@ def run_ours(args):
                     "ms_per_step": fb_ms / fb_steps, "gpu_launches": 2 * fb_steps,
                     "loss": "-(torso x displacement); gradients w.r.t. the action sequence and the initial state"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": fl.get("traffic_bytes_per_launch"),
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": measured_traffic(f"quadruped_{N}x{T}") if world == 1 else None,
+                     "algorithmic_bytes": algorithmic_bytes,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                      "flops_per_env_step": flops_per_envstep, "kernel_ms": kern_ms},
         "clocks": clk.summary(),
