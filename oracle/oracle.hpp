@@ -557,6 +557,36 @@ template <class T> inline void capsule_box(const V3<T>& P, const V3<T>& d, doubl
 // Every listed pair, every substep (Sec. 7.2: naive pair enumeration).
 template <class T> inline void detect(const System& s, const Body<T>* qp, const Frame<T>* fr,
                                       std::vector<Contact<T>>& out) {
+  // World geometry of a collider, computed once per substep however many
+  // pairs it is in (a property of the collider's body, not of the pair):
+  // capsule end points P, Q (Q = P for a sphere); box axes Rb (body rotation
+  // times collider rotation, as columns) and centre.
+  const int C = s.C;
+  std::vector<V3<T>> wP(C), wQ(C), wc(C);
+  std::vector<M3<T>> wR(C);
+  std::vector<char> have(C, 0);
+  auto world = [&](int c) {
+    if (have[c]) return;
+    have[c] = 1;
+    const int b = s.col_body[c];
+    if (s.col_type[c] == COL_CAPSULE) {
+      double e0[3], e1[3];
+      capsule_local(s, c, e0, e1);
+      wP[c] = qp[b].x + mulc(fr[b].R, e0);
+      wQ[c] = capsule_half(s, c) > 0.0 ? qp[b].x + mulc(fr[b].R, e1) : wP[c];
+    } else if (s.col_type[c] == COL_BOX) {
+      double ex[3] = {1, 0, 0}, ey[3] = {0, 1, 0}, ez[3] = {0, 0, 1}, cx[3], cy[3], cz[3];
+      cq_rotate(&s.col_rot[4 * c], ex, cx);
+      cq_rotate(&s.col_rot[4 * c], ey, cy);
+      cq_rotate(&s.col_rot[4 * c], ez, cz);
+      V3<T> X = mulc(fr[b].R, cx), Y = mulc(fr[b].R, cy), Z = mulc(fr[b].R, cz);
+      M3<T>& Rb = wR[c];
+      Rb.m[0][0] = X.x; Rb.m[0][1] = Y.x; Rb.m[0][2] = Z.x;
+      Rb.m[1][0] = X.y; Rb.m[1][1] = Y.y; Rb.m[1][2] = Z.y;
+      Rb.m[2][0] = X.z; Rb.m[2][1] = Y.z; Rb.m[2][2] = Z.z;
+      wc[c] = qp[b].x + mulc(fr[b].R, &s.col_pos[3 * c]);
+    }
+  };
   for (int k = 0; k < s.P; ++k) {
     int ca = s.pair_a[k], cbk = s.pair_b[k];
     // order: the static plane, if any, second; a box second against a capsule
@@ -569,10 +599,9 @@ template <class T> inline void detect(const System& s, const Body<T>* qp, const 
       double p0[3], n[3];
       plane_of(s, cbk, p0, n);
       if (ta == COL_CAPSULE) {
-        double e0[3], e1[3];
-        capsule_local(s, ca, e0, e1);
-        sphere_plane(qp[ba].x + mulc(fr[ba].R, e0), s.radius[ca], p0, n, ba, mu, el, out);
-        if (capsule_half(s, ca) > 0.0) sphere_plane(qp[ba].x + mulc(fr[ba].R, e1), s.radius[ca], p0, n, ba, mu, el, out);
+        world(ca);
+        sphere_plane(wP[ca], s.radius[ca], p0, n, ba, mu, el, out);
+        if (capsule_half(s, ca) > 0.0) sphere_plane(wQ[ca], s.radius[ca], p0, n, ba, mu, el, out);
       } else if (ta == COL_BOX) {
         const double* he = &s.half[3 * ca];
         for (int m = 0; m < 8; ++m) {
@@ -584,12 +613,11 @@ template <class T> inline void detect(const System& s, const Body<T>* qp, const 
         }
       }
     } else if (ta == COL_CAPSULE && tb == COL_CAPSULE) {
-      double a0[3], a1[3], b0[3], b1[3];
-      capsule_local(s, ca, a0, a1);
-      capsule_local(s, cbk, b0, b1);
-      V3<T> P1 = qp[ba].x + mulc(fr[ba].R, a0), Q1 = qp[ba].x + mulc(fr[ba].R, a1);
-      V3<T> P2 = qp[bb].x + mulc(fr[bb].R, b0), Q2 = qp[bb].x + mulc(fr[bb].R, b1);
-      V3<T> d1 = Q1 - P1, d2 = Q2 - P2;
+      world(ca);
+      world(cbk);
+      const V3<T>& P1 = wP[ca];
+      const V3<T>& P2 = wP[cbk];
+      V3<T> d1 = wQ[ca] - P1, d2 = wQ[cbk] - P2;
       T sp, tp;
       segment_closest(P1, d1, P2, d2, sp, tp);
       V3<T> c1 = P1 + sp * d1, c2 = P2 + tp * d2;
@@ -602,21 +630,9 @@ template <class T> inline void detect(const System& s, const Body<T>* qp, const 
       V3<T> p = T(0.5) * ((c1 - T(s.radius[ca]) * n) + (c2 + T(s.radius[cbk]) * n));
       out.push_back(Contact<T>{n, p, depth, ba, bb, mu, el});
     } else if (ta == COL_CAPSULE && tb == COL_BOX) {
-      double a0[3], a1[3];
-      capsule_local(s, ca, a0, a1);
-      V3<T> P = qp[ba].x + mulc(fr[ba].R, a0), Q = qp[ba].x + mulc(fr[ba].R, a1);
-      // box frame = body rotation * collider rotation
-      double ex[3] = {1, 0, 0}, ey[3] = {0, 1, 0}, ez[3] = {0, 0, 1}, cx[3], cy[3], cz[3];
-      cq_rotate(&s.col_rot[4 * cbk], ex, cx);
-      cq_rotate(&s.col_rot[4 * cbk], ey, cy);
-      cq_rotate(&s.col_rot[4 * cbk], ez, cz);
-      V3<T> X = mulc(fr[bb].R, cx), Y = mulc(fr[bb].R, cy), Z = mulc(fr[bb].R, cz);
-      M3<T> Rb;
-      Rb.m[0][0] = X.x; Rb.m[0][1] = Y.x; Rb.m[0][2] = Z.x;
-      Rb.m[1][0] = X.y; Rb.m[1][1] = Y.y; Rb.m[1][2] = Z.y;
-      Rb.m[2][0] = X.z; Rb.m[2][1] = Y.z; Rb.m[2][2] = Z.z;
-      V3<T> cb = qp[bb].x + mulc(fr[bb].R, &s.col_pos[3 * cbk]);
-      capsule_box(P, Q - P, s.radius[ca], ba, cb, Rb, &s.half[3 * cbk], bb, mu, el, out);
+      world(ca);
+      world(cbk);
+      capsule_box(wP[ca], wQ[ca] - wP[ca], s.radius[ca], ba, wc[cbk], wR[cbk], &s.half[3 * cbk], bb, mu, el, out);
     }
   }
 }

@@ -86,8 +86,8 @@ __device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, 
   kinematic(bp, S.h, s);
   const Frame f = make_frame(bp, s);
   if (bp.flags & kPublish) {
-    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
-    else publish<false>(gm, b, lane, s, f);
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f, bp);
+    else publish<false>(gm, b, lane, s, f, bp);
   }
   group_sync(bar, nthr);
   Wrench wr{zero3(), zero3()};
@@ -123,8 +123,8 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   kinematic(bp, h, s);
   const Frame f = make_frame(bp, s);
   if (bp.flags & kPublish) {
-    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
-    else publish<false>(gm, b, lane, s, f);
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f, bp);
+    else publish<false>(gm, b, lane, s, f, bp);
   }
   group_sync(bar, nthr);
   // ---- forward recompute: phase J

@@ -259,6 +259,7 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   };
   // pairs
   std::vector<PairP> pairs;
+  std::vector<int> body_pcol(B, -1), body_multi(B, 0);  // a body's collider in pairs; several of them
   for (int k = 0; k < P; ++k) {
     int ca = d.pair_a[k], cb = d.pair_b[k];
     REQUIRE(ca >= 0 && ca < C && cb >= 0 && cb < C && ca != cb, "pair: collider index out of range");
@@ -339,6 +340,9 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
       const int idx = (int)pairs.size();
       pairs.push_back(pr);
       for (int side = 0; side < 2; ++side) {
+        const int bi = side == 0 ? ba : bb, ci = side == 0 ? ca : cb;
+        if (body_pcol[bi] < 0) body_pcol[bi] = ci;
+        else if (body_pcol[bi] != ci) body_multi[bi] = 1;
         BodyP& bp = bodies[side == 0 ? ba : bb];
         REQUIRE(bp.n_bpairs < BRAX_MAX_BODY_PAIRS, "body: more than BRAX_MAX_BODY_PAIRS body-body pairs");
         bp.bpair[bp.n_bpairs++] = (idx << 1) | side;
@@ -347,6 +351,37 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
     }
   }
   const int Pb = (int)pairs.size();
+  // bodies with exactly one collider in pairs publish its world geometry
+  for (int b = 0; b < B; ++b) {
+    BodyP& bp = bodies[b];
+    bp.gtype = -1;
+    const int c = body_pcol[b];
+    if (c < 0 || body_multi[b]) continue;
+    if (d.col_type[c] == BRAX_CAPSULE) {
+      double e0[3], e1[3];
+      capsule_local(c, e0, e1);
+      bp.gtype = 0;
+      for (int i = 0; i < 3; ++i) {
+        bp.g0[i] = (float)e0[i];
+        bp.g1[i] = (float)e1[i];
+      }
+    } else {
+      double q[4] = {d.col_rot[4 * c], d.col_rot[4 * c + 1], d.col_rot[4 * c + 2], d.col_rot[4 * c + 3]};
+      dq_normalize(q);
+      double Rm[3][3];
+      dq_matrix(q, Rm);
+      bp.gtype = 1;
+      for (int i = 0; i < 3; ++i) {
+        bp.g0[i] = d.col_pos[3 * c + i];
+        for (int j = 0; j < 3; ++j) bp.g1[3 * i + j] = (float)Rm[i][j];
+      }
+    }
+  }
+  for (int k = 0; k < Pb; ++k) {
+    pairs[k].geo = 0;
+    if (bodies[pairs[k].ba].gtype >= 0) pairs[k].geo |= 1;
+    if (bodies[pairs[k].bb].gtype >= 0) pairs[k].geo |= 2;
+  }
   S.B = B;
   S.J = J;
   S.A = A;

@@ -32,7 +32,7 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
     const bool parent_of = bp.tree_slot >= 0;
     const int my_n = 32 * (1 + bp.n_children);
     if (parent_of) {
-      publish<false>(gm, b, lane, s, f);
+      publish<false>(gm, b, lane, s, f, bp);
       bar_arrive(2 + 2 * bp.tree_slot, my_n);
     }
     // the own contacts need only the own state: do them while the parent publishes
@@ -55,8 +55,8 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
     return counted;
   }
   if (bp.flags & kPublish) {
-    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f);
-    else publish<false>(gm, b, lane, s, f);
+    if (kGeneral && (bp.flags & kInPair)) publish<true>(gm, b, lane, s, f, bp);
+    else publish<false>(gm, b, lane, s, f, bp);
   }
   group_sync(bar, nthr);
   Wrench wr{mk3(0.f, 0.f, 0.f), mk3(0.f, 0.f, 0.f)};

@@ -61,6 +61,13 @@ struct BodyP {
   float frame_p[4], frame_c[4];  // joint frame quaternions (normalised)
   int32_t dof_offset;            // first joint-angle index of the parent joint
   int32_t tree_slot;             // index among bodies with children (-1: none); names its two tree barriers
+  // The body's collider in body-body pairs when it has exactly one (-1: none
+  // or several): its world geometry is computed once per substep and
+  // published (capsule: g0, g1 = segment end points; box: g0 = centre,
+  // g1 = axes, row-major), instead of once per pair.
+  int32_t gtype;  // -1, 0 capsule, 1 box
+  float g0[3];
+  float g1[9];
 };
 
 enum PairType : int32_t { kCapsuleCapsule = 0, kCapsuleBox = 1 };
@@ -71,7 +78,7 @@ enum PairType : int32_t { kCapsuleCapsule = 0, kCapsuleBox = 1 };
 struct PairP {
   int32_t type;
   int32_t ba, bb;
-  int32_t pad;
+  int32_t geo;  // bit 0 / bit 1: body a's / body b's collider geometry is published by the body
   float mu, e;
   float ra, rb;
   float a0[3], a1[3];
@@ -136,7 +143,7 @@ __host__ __device__ inline int blob_bytes(int B, int P, int n_planes) {
 __host__ __device__ inline int blob_pair_bytes(int B) { return (int)sizeof(SysP2) + B * (int)sizeof(BodyP2); }
 
 // Shared memory of one group of 32 environments (floats), after the blob.
-constexpr int kPubFields = 24;    // x[3], R[9], v[3], w[3], Ii[6]: six float4 per lane
+constexpr int kPubFields = 36;    // x[3], R[9], v[3], w[3], Ii[6], pair geometry[12]: nine float4 per lane
 constexpr int kReactFields = 8;   // F[3], tau[3], 2 pad: two float4 per lane
 constexpr int kSlotFields = 8;    // J[3], p[3], active flag, pad: two float4 per lane
 // Tree barriers (one group per block): parent slot k owns named barrier

@@ -97,8 +97,25 @@ __device__ __forceinline__ Frame make_frame(const BodyP& bp, const Body& s) {
   return f;
 }
 
+// World geometry of a body's pair collider (the expressions pair_forward
+// and pair_bwd use): capsule segment start P and direction d; box axes Rb
+// (row-major, R_body * R_collider) and centre cb.
+__device__ __forceinline__ void capsule_world(const M3& R, V3 x, const float* e0, const float* e1, V3& P, V3& d) {
+  P = x + mulc(R, e0);
+  d = mulc(R, e1) - mulc(R, e0);
+}
+__device__ __forceinline__ void box_world(const M3& R, V3 x, const float* c0, const float* bR, M3& Rb, V3& cb) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Rb.m[3 * i + j] = fmaf(R.m[3 * i + 0], bR[0 * 3 + j], fmaf(R.m[3 * i + 1], bR[1 * 3 + j], R.m[3 * i + 2] * bR[2 * 3 + j]));
+  cb = x + mulc(R, c0);
+}
+
 template <bool kIi>
-__device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Body& s, const Frame& f) {
+__device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Body& s, const Frame& f,
+                                        const BodyP& bp) {
   float4* p = gm.pub4(b, 0) + lane;
   p[0] = make_float4(s.x.x, s.x.y, s.x.z, f.R.m[0]);
   p[32] = make_float4(f.R.m[1], f.R.m[2], f.R.m[3], f.R.m[4]);
@@ -107,9 +124,43 @@ __device__ __forceinline__ void publish(GroupMem& gm, int b, int lane, const Bod
   if (kIi) {
     p[128] = make_float4(s.w.y, s.w.z, f.Ii.a[0], f.Ii.a[1]);
     p[160] = make_float4(f.Ii.a[2], f.Ii.a[3], f.Ii.a[4], f.Ii.a[5]);
+    if (bp.gtype == 0) {
+      V3 P, d;
+      capsule_world(f.R, s.x, bp.g0, bp.g1, P, d);
+      p[192] = make_float4(P.x, P.y, P.z, d.x);
+      st2(p + 224, d.y, d.z);
+    } else if (bp.gtype == 1) {
+      M3 Rb;
+      V3 cb;
+      box_world(f.R, s.x, bp.g0, bp.g1, Rb, cb);
+      p[192] = make_float4(cb.x, cb.y, cb.z, Rb.m[0]);
+      p[224] = make_float4(Rb.m[1], Rb.m[2], Rb.m[3], Rb.m[4]);
+      p[256] = make_float4(Rb.m[5], Rb.m[6], Rb.m[7], Rb.m[8]);
+    }
   } else {
     st2(p + 128, s.w.y, s.w.z);
   }
+}
+__device__ __forceinline__ void read_capsule_world(GroupMem& gm, int b, int lane, V3& P, V3& d) {
+  const float4* p = gm.pub4(b, 6) + lane;
+  const float4 c0 = p[0];
+  const float2 c1 = ld2(p + 32);
+  P = mk3(c0.x, c0.y, c0.z);
+  d = mk3(c0.w, c1.x, c1.y);
+}
+__device__ __forceinline__ void read_box_world(GroupMem& gm, int b, int lane, M3& Rb, V3& cb) {
+  const float4* p = gm.pub4(b, 6) + lane;
+  const float4 c0 = p[0], c1 = p[32], c2 = p[64];
+  cb = mk3(c0.x, c0.y, c0.z);
+  Rb.m[0] = c0.w;
+  Rb.m[1] = c1.x;
+  Rb.m[2] = c1.y;
+  Rb.m[3] = c1.z;
+  Rb.m[4] = c1.w;
+  Rb.m[5] = c2.x;
+  Rb.m[6] = c2.y;
+  Rb.m[7] = c2.z;
+  Rb.m[8] = c2.w;
 }
 
 struct Pub {
@@ -467,16 +518,26 @@ __device__ __forceinline__ float seg_box_param(V3 Pl, V3 dl, const float* he) {
 // write (J, p, 1) to the pair's slot, else (0, 0, 0).
 __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, const PairP& pr, GroupMem& gm,
                                             int k, int lane) {
-  const Pub A = read_pub(gm, pr.ba, lane);
-  const Pub Bq = read_pub(gm, pr.bb, lane);
-  const V3 P1 = A.x + mulc(A.R, pr.a0);
-  const V3 d1 = mulc(A.R, pr.a1) - mulc(A.R, pr.a0);
+  // detection needs only the colliders' world geometry: published by the
+  // bodies (computed once per substep), else computed here
+  V3 P1, d1;
+  if (pr.geo & 1) {
+    read_capsule_world(gm, pr.ba, lane, P1, d1);
+  } else {
+    const Pub A = read_pub(gm, pr.ba, lane);
+    capsule_world(A.R, A.x, pr.a0, pr.a1, P1, d1);
+  }
   V3 n, p;
   float depth;
   bool hit = false;
   if (pr.type == kCapsuleCapsule) {
-    const V3 P2 = Bq.x + mulc(Bq.R, pr.b0);
-    const V3 d2 = mulc(Bq.R, pr.b1) - mulc(Bq.R, pr.b0);
+    V3 P2, d2;
+    if (pr.geo & 2) {
+      read_capsule_world(gm, pr.bb, lane, P2, d2);
+    } else {
+      const Pub Bq = read_pub(gm, pr.bb, lane);
+      capsule_world(Bq.R, Bq.x, pr.b0, pr.b1, P2, d2);
+    }
     float sp, tp;
     segment_closest(P1, d1, P2, d2, sp, tp);
     const V3 c1 = fma3(sp, d1, P1), c2 = fma3(tp, d2, P2);
@@ -493,13 +554,13 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
   } else {
     // box frame: rotation Rb = R_b * bR, centre cb
     M3 Rb;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Rb.m[3 * i + j] = fmaf(Bq.R.m[3 * i + 0], pr.bR[0 * 3 + j],
-                               fmaf(Bq.R.m[3 * i + 1], pr.bR[1 * 3 + j], Bq.R.m[3 * i + 2] * pr.bR[2 * 3 + j]));
-    const V3 cb = Bq.x + mulc(Bq.R, pr.b0);
+    V3 cb;
+    if (pr.geo & 2) {
+      read_box_world(gm, pr.bb, lane, Rb, cb);
+    } else {
+      const Pub Bq = read_pub(gm, pr.bb, lane);
+      box_world(Bq.R, Bq.x, pr.b0, pr.bR, Rb, cb);
+    }
     const V3 Pl = mulT(Rb, P1 - cb);
     const V3 dl = mulT(Rb, d1);
     const float* he = pr.b1;
@@ -542,6 +603,8 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
     sl[32] = make_float4(0.f, 0.f, 0.f, 0.f);
     return 0;
   }
+  const Pub A = read_pub(gm, pr.ba, lane);
+  const Pub Bq = read_pub(gm, pr.bb, lane);
   const BodyP& ba = bodies[pr.ba];
   const BodyP& bb = bodies[pr.bb];
   const S6 Ia = read_pub_Ii(gm, pr.ba, lane);
