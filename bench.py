@@ -66,10 +66,10 @@ def kernel_sources_digest():
     return h.hexdigest()
 
 
-def measured_traffic(key):
+def measured_traffic(key, path=None):
     """DRAM bytes per launch of the dominant kernel from one ncu capture
     (data/traffic.json), or None when the kernel sources changed since."""
-    p = os.path.join(ROOT, "paper_2106_13281_gb300", "data", "traffic.json")
+    p = path or os.path.join(ROOT, "paper_2106_13281_gb300", "data", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -233,13 +233,14 @@ def run_ours(args):
     h_state0 = state0.cpu().pin_memory()
     h_actions = actions.cpu().pin_memory()
     h_out = torch.empty_like(h_state0).pin_memory()
-    d_state0, d_actions = torch.empty_like(state0), torch.empty_like(actions)
+
+    # the actions stream in on a copy stream, 100 steps at a time, while the
+    # previous 100 steps run (BraxSystem.rollout_streamed)
+    e2e_bufs = {}
+    e2e_chunk = 100
 
     def e2e_step():
-        d_state0.copy_(h_state0, non_blocking=True)
-        d_actions.copy_(h_actions, non_blocking=True)
-        sysm.rollout(d_state0, d_actions, state_T=state_T)
-        h_out.copy_(state_T, non_blocking=True)
+        return sysm.rollout_streamed(h_state0, h_actions, h_out, chunk_steps=e2e_chunk, bufs=e2e_bufs)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -311,7 +312,9 @@ def run_ours(args):
                    "envs": N, "steps_per_rollout": T, "substeps": int(d["substeps"]), "dt": float(d["dt"]),
                    "l2": "inputs larger than L2 (actions %.2f GB per rollout)" % (actions.numel() * 4 / 1e9),
                    "parallelism": f"env shards x{world}"},
-        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "BraxSystem.rollout_streamed (pinned host inputs, %d-step chunks overlapped with compute)"
+                       % e2e_chunk, "gpu_launches_per_step": math.ceil(T / e2e_chunk)},
         "gpu_launches": args.steps,
         "fwd_bwd": {"value": fwd_bwd_value, "unit": "env-steps/s", "steps": fb_steps, "checkpoint_every": K,
                     "ms_per_step": fb_ms / fb_steps, "gpu_launches": 2 * fb_steps,

@@ -230,3 +230,24 @@ def test_pair_launch_rejected_for_general_systems(brax):
     with pytest.raises(BraxError):
         sysm.set_pair_launch(1, 1, 0)
     sysm.set_pair_launch(0)
+
+
+@pytest.mark.parametrize("name,drop", [("quadruped", 0.38), ("pendulum", 0.0)])
+def test_rollout_streamed_equals_one_launch(brax, name, drop):
+    """Actions streamed from pinned host memory in chunks (ragged last chunk)
+    give bitwise the state of one launch over all steps."""
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    N, T = 100, 25
+    st, _ = initial(d, N, 13, drop=drop)
+    a = f32(S.actions(d, N, T, 14))
+    ref = sysm.rollout(cuda(st), cuda(a))["state_T"].cpu()
+    hs = torch.from_numpy(f32(st)).pin_memory()
+    ha = torch.from_numpy(a).pin_memory()
+    out = torch.empty((N, sysm.B, 13)).pin_memory()
+    bufs = {}
+    for chunk in (10, 7, 25, 100):
+        n = sysm.rollout_streamed(hs, ha, out, chunk_steps=chunk, bufs=bufs)
+        torch.cuda.synchronize()
+        assert n == math.ceil(T / min(chunk, T))
+        assert torch.equal(out, ref), chunk
