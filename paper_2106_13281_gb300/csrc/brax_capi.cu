@@ -525,8 +525,8 @@ void pool_release(int device, int off) {
     }
 }
 
-// Smallest launch bound that admits the block (measured fastest for the
-// quadruped: (288, 3)).
+// Default launch-bounds variant: the smallest that admits the block (the
+// autotuner may pick another).
 int pick_variant(int threads) {
   static const int order[4] = {3, 0, 1, 2};
   for (int v : order)

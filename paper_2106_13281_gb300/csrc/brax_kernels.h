@@ -7,7 +7,9 @@
 
 namespace brax {
 
-// variant: 0 = (384 threads, 2 blocks/SM), 1 = (640, 1), 2 = (1024, 1) launch bounds
+// Launch-bounds variants (max threads per block, min blocks per SM):
+// 0 = (384, 2), 1 = (576, 1), 2 = (1024, 1), 3 = (288, 3); the autotuner
+// (brax_tune.cu) picks one per system.
 cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                            cudaStream_t st);
 // Copy a parameter blob into the constant pool of each kernel translation unit.
