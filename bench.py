@@ -487,6 +487,7 @@ def run_workload(args):
         batch = BraxBatch(systems, ns)
         st, a, gT = torch.cat(sts), torch.cat(acs), torch.cat(gts)
         K = 10
+        warps, _ = batch.autotune(st, a, T, K=K, reverse=True)
         ws = torch.empty((batch.workspace_size(T, K),), device="cuda", dtype=torch.uint8)
 
         def fwd():
@@ -504,7 +505,8 @@ def run_workload(args):
                       "fwd_only": {"value": sum(ns) * T / ms_f * 1e3, "ms_per_step": ms_f,
                                    "roofline": roof(fl, sum(ns) * T, ms_f)},
                       "config": {"workload": "32768 pendulum + 16384 quadruped + 8192 biped + 8192 arm+box, "
-                                             "200 steps, checkpoints every 10", "checkpoint_every": K}})
+                                             "200 steps, checkpoints every 10", "checkpoint_every": K},
+                      "tuning": {"warps_per_block": warps}})
     for ln in lines:
         ln.update({"n_gpus": 1, "warmup": args.warmup, "dtype": "f32", "data": "synthetic", "higher_is_better": True})
         print(json.dumps(ln), flush=True)

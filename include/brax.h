@@ -245,6 +245,15 @@ typedef struct {
 } brax_tune_result;
 int brax_autotune(brax_system* sys, int64_t n_envs, int32_t T, const float* state0, const float* actions,
                   int32_t flags, size_t mem_budget, void* stream, brax_tune_result* out);
+/* Heterogeneous batch: picks the block size (warps per thread block; each
+ * system packs floor(warps / n_bodies) groups of 32 environments into a
+ * block) by timing the batch's forward rollout on min(T, 10) steps of the
+ * caller's arrays (with BRAX_TUNE_REVERSE: forward with checkpoints every K
+ * steps plus the reverse pass, on min(T, 20) steps).  Applies the fastest;
+ * *warps_out and *ms_out (its time) may be NULL.  Allocates temporary device
+ * memory and synchronizes `stream`. */
+int brax_batch_autotune(brax_batch* batch, int32_t T, int32_t K, const float* state0, const float* actions,
+                        int32_t flags, void* stream, int32_t* warps_out, float* ms_out);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* brax_last_error(void);

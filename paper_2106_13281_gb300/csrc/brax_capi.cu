@@ -469,12 +469,6 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
 
 }  // namespace
 
-struct brax_batch {
-  std::vector<const brax_system*> sys;
-  std::vector<int64_t> n_envs;
-  int warps = 0;  // warps per thread block
-};
-
 namespace {
 
 size_t group_bytes(const brax_system* s) { return (size_t)group_floats(s->B, s->P) * sizeof(float); }

@@ -25,6 +25,12 @@ struct brax_system {
   int bwd_variant = -1;  // launch-bounds variant of the reverse kernel (-1: smallest that fits)
 };
 
+struct brax_batch {
+  std::vector<const brax_system*> sys;
+  std::vector<int64_t> n_envs;
+  int warps = 0;  // warps per thread block
+};
+
 extern "C" int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant);
 extern "C" int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant);
 

@@ -205,3 +205,69 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
   if (e != cudaSuccess) return tune_fail(BRAX_ERR_CUDA, std::string("brax_autotune: ") + cudaGetErrorString(e));
   return BRAX_OK;
 }
+
+extern "C" int brax_batch_autotune(brax_batch* b, int32_t T, int32_t K, const float* state0, const float* actions,
+                                   int32_t flags, void* stream, int32_t* warps_out, float* ms_out) {
+  if (!b || T < 1 || K < 1 || !state0 || (flags & ~(BRAX_TUNE_FORWARD | BRAX_TUNE_REVERSE)) != 0 || flags == 0)
+    return tune_fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_autotune: bad arguments");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int maxB = 0;
+  for (const brax_system* s : b->sys) maxB = std::max(maxB, s->B);
+  const bool rev = (flags & BRAX_TUNE_REVERSE) != 0;
+  const int Ts = std::min(T, rev ? 20 : 10);
+  const int Ke = std::min(K, Ts);
+  int64_t st_n = 0, ck_n = 0, act_n = 0;
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    st_n += b->n_envs[i] * b->sys[i]->B * 13;
+    ck_n += (int64_t)((Ts + Ke - 1) / Ke) * b->n_envs[i] * b->sys[i]->B * 13;
+    act_n += (int64_t)Ts * b->n_envs[i] * std::max(b->sys[i]->A, 1);
+  }
+  const int saved = b->warps;
+  size_t ws_max = 0;
+  std::vector<int> cands;
+  for (int w = maxB; w <= 32; ++w) {
+    b->warps = w;
+    size_t ws = 0;
+    if (rev && brax_batch_workspace_size(b, Ts, Ke, &ws) != BRAX_OK) continue;
+    ws_max = std::max(ws_max, ws);
+    cands.push_back(w);
+  }
+  DeviceBuffer stT, ck, ws, gst, gs0, gact;
+  if (stT.alloc(st_n * sizeof(float)) != cudaSuccess ||
+      (rev && (ck.alloc(ck_n * sizeof(float)) != cudaSuccess || ws.alloc(ws_max) != cudaSuccess ||
+               gst.alloc(st_n * sizeof(float)) != cudaSuccess || gs0.alloc(st_n * sizeof(float)) != cudaSuccess ||
+               gact.alloc(act_n * sizeof(float)) != cudaSuccess))) {
+    b->warps = saved;
+    return tune_fail(BRAX_ERR_OUT_OF_MEMORY, "brax_batch_autotune: cudaMalloc");
+  }
+  if (rev) cudaMemsetAsync(gst.p, 0, st_n * sizeof(float), st);
+  Events ev;
+  float best = -1.f;
+  int pick = saved;
+  for (int w : cands) {
+    b->warps = w;
+    const float ms = time_best(
+        [&] {
+          int rc = brax_batch_rollout(b, Ts, Ke, state0, actions, static_cast<float*>(stT.p),
+                                      rev ? static_cast<float*>(ck.p) : nullptr, nullptr, stream);
+          if (rc == BRAX_OK && rev)
+            rc = brax_batch_rollout_backward(b, Ts, Ke, state0, actions, static_cast<float*>(ck.p),
+                                             static_cast<float*>(gst.p), nullptr, static_cast<float*>(gact.p),
+                                             static_cast<float*>(gs0.p), ws.p, ws_max, stream);
+          return rc;
+        },
+        st, ev);
+    cudaGetLastError();
+    if (ms >= 0.f && (best < 0.f || ms < best)) {
+      best = ms;
+      pick = w;
+    }
+  }
+  b->warps = pick;
+  if (best < 0.f) return tune_fail(BRAX_ERR_CUDA, "brax_batch_autotune: no configuration ran");
+  if (warps_out) *warps_out = pick;
+  if (ms_out) *ms_out = best;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return tune_fail(BRAX_ERR_CUDA, std::string("brax_batch_autotune: ") + cudaGetErrorString(e));
+  return BRAX_OK;
+}

@@ -313,6 +313,15 @@ class BraxBatch:
         check(self._L.brax_batch_workspace_size(self._h, T, K, C.byref(b)))
         return b.value
 
+    def autotune(self, state0, actions, T, K=10, reverse=False):
+        """Pick the block size (warps per block) by timing this batch's own
+        arrays (brax_batch_autotune); returns (warps, ms)."""
+        w, ms = C.c_int32(), C.c_float()
+        flags = BRAX_TUNE_FORWARD | (BRAX_TUNE_REVERSE if reverse else 0)
+        check(self._L.brax_batch_autotune(self._h, T, K, _ptr(state0), _ptr(actions), flags, _stream(), C.byref(w),
+                                          C.byref(ms)))
+        return w.value, ms.value
+
     def rollout_backward(self, state0, actions, checkpoints, g_state_T, T, K=1, g_torso=None, workspace=None):
         nbytes = self.workspace_size(T, K)
         if workspace is None or workspace.numel() < nbytes:

@@ -112,3 +112,20 @@ def test_batch_cuda_graph(batch_setup):
     torch.cuda.synchronize()
     assert torch.equal(out["state_T"], eager["state_T"])
     assert torch.equal(gs, e_gs) and torch.equal(ga, e_ga)
+
+
+def test_batch_autotune_keeps_results(batch_setup):
+    """The batch autotuner changes only the block size: every system's slice
+    still equals its solo launch."""
+    descs, systems, n_envs, batch = batch_setup
+    T, K = 4, 2
+    states, acts = make_inputs(descs, n_envs, T, 91)
+    warps, ms = batch.autotune(cat(states), cat(acts), T, K=K, reverse=True)
+    assert max(s.B for s in systems) <= warps <= 32 and ms > 0
+    out = batch.rollout(cat(states), cat(acts), T, K=K, checkpoints=True)
+    for i, s in enumerate(systems):
+        so, ao, to, co = batch.offsets(T, K, i)
+        n = n_envs[i]
+        solo = s.rollout(cuda(states[i]), cuda(acts[i]), K=K, checkpoints=True)
+        got = out["state_T"][so:so + n * s.B * 13].view(n, s.B, 13)
+        assert torch.allclose(got, solo["state_T"], rtol=1e-6, atol=1e-6), NAMES[i]
