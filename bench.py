@@ -295,6 +295,9 @@ def run_ours(args):
     fl = alg_flops("quadruped")
     flops_per_envstep = fl["flops_per_env_step"]
     achieved_tflops = flops_per_envstep * envsteps / (kern_ms / 1e3) / 1e12
+    # forward + reverse: the forward, one forward recompute and the tape's reverse-op count
+    fb_flops = 2 * flops_per_envstep + fl["reverse_flops_per_env_step"]
+    fb_tflops = fb_flops * envsteps / (fb_ms / fb_steps / 1e3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -318,6 +321,9 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "fwd_bwd": {"value": fwd_bwd_value, "unit": "env-steps/s", "steps": fb_steps, "checkpoint_every": K,
                     "ms_per_step": fb_ms / fb_steps, "gpu_launches": 2 * fb_steps,
+                    "roofline": {"bound": "alu", "achieved": fb_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": fb_tflops / FP32_PEAK_TFLOPS, "flops_per_env_step": fb_flops,
+                                 "note": "forward + one forward recompute + the oracle tape's reverse-op count"},
                     "loss": "-(torso x displacement); gradients w.r.t. the action sequence and the initial state"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS,
@@ -464,8 +470,10 @@ def run_workload(args):
 
             ms = _timed(fb2, args.warmup, steps)
             sysm.sync_status()
+            fq = alg_flops("quadruped")
             lines.append({"metric": "env-steps/s fwd+bwd, 9-body quadruped adjoint @4096 envs",
                           "value": N * T / ms * 1e3, "unit": "env-steps/s", "ms_per_step": ms, "steps": steps,
+                          "roofline": roof(2 * fq["flops_per_env_step"] + fq["reverse_flops_per_env_step"], N * T, ms),
                           "config": {"workload": f"quadruped adjoint, 4096 envs x {T} steps, loss -torso x "
                                                  "displacement (+ action penalty, differentiated by torch)",
                                      "checkpoint_every": K},

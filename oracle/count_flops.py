@@ -1,5 +1,7 @@
 """Write paper_2106_13281_gb300/data/alg_flops.json: the algorithmic flop count
-per environment step of each scene, from the oracle's flop-counting scalar
+per environment step of each scene (forward, and the reverse pass as the
+tape's reverse-op count: 2 flops per tape edge plus the flops that formed
+the local partials), from the oracle's flop-counting scalar
 (add/sub/mul/div/sqrt/atan2/min/max = 1 flop; every listed collision pair is
 detected every substep; contact response counted for active contacts only).
 
@@ -39,6 +41,10 @@ def main():
         a = S.actions(d, N, T, seed).astype(np.float64)
         counts, n_active = orc.flops(d, st, a)
         es = N * T
+        # reverse pass: the tape's reverse-op count on a shorter slice of the
+        # same sample (the tape of a long rollout is large)
+        Nr, Tr = min(N, 8), min(T, 50)
+        rev, nodes = orc.reverse_flops(d, st[:Nr], a[:Tr, :Nr])
         total = sum(counts.values())
         resp = counts["response"]
         out[name] = {
@@ -47,8 +53,10 @@ def main():
             "active_contacts_per_substep": n_active / es / d["substeps"],
             "response_flops_per_active_contact": resp / n_active if n_active else 0.0,
             "sample": f"{N} envs x {T} steps, seed {seed}",
+            "reverse_flops_per_env_step": rev / (Nr * Tr),
+            "reverse_sample": f"{Nr} envs x {Tr} steps (tape: {nodes / (Nr * Tr):.0f} nodes per env-step)",
         }
-        print(name, round(total / es), "flops/env-step", flush=True)
+        print(name, round(total / es), "flops/env-step forward,", round(rev / (Nr * Tr)), "reverse", flush=True)
     path = os.path.join(ROOT, "paper_2106_13281_gb300", "data", "alg_flops.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)

@@ -121,6 +121,7 @@ def lib():
             L.orc_rollout.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
             L.orc_flops.argtypes = [P, i64, i32, P, P, P, P]
             L.orc_vjp.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
+            L.orc_reverse_flops.argtypes = [P, i64, i32, P, P, P, i32]
             L.orc_jvp.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
             L.orc_default_qp.argtypes = [P, i64, P, P, P, P]
             L.orc_joint_angles.argtypes = [P, i64, P, P]
@@ -185,6 +186,18 @@ def flops(system, state0, actions):
     na = np.zeros(1, dtype=np.int64)
     lib().orc_flops(C.byref(s.c), state0.shape[0], actions.shape[0], _p(state0), _p(actions), _p(counts), _p(na))
     return dict(zip(FLOP_CATEGORIES, counts.tolist())), int(na[0])
+
+
+def reverse_flops(system, state0, actions, n_threads=0):
+    """Algorithmic flops of the reverse pass of a rollout (the tape's
+    reverse-op count), summed over environments, and the tape's node count."""
+    s = _sys(system)
+    state0 = _f64(state0)
+    actions = _f64(actions)
+    out = np.zeros(2, dtype=np.int64)
+    lib().orc_reverse_flops(C.byref(s.c), state0.shape[0], actions.shape[0], _p(state0), _p(actions), _p(out),
+                            _threads(n_threads))
+    return int(out[0]), int(out[1])
 
 
 def vjp(system, state0, actions, g_state_T, g_torso=None, n_threads=0):

@@ -246,6 +246,38 @@ int orc_vjp(const orc_desc* d, int64_t N, int32_t T, const double* state0, const
   return 0;
 }
 
+// Reverse-op count of a rollout's tape (the algorithmic flops of the reverse
+// pass): out[0] = 2 flops per tape edge (multiply and accumulate) + the
+// flops that formed the local partials; out[1] = tape nodes.  Summed over
+// environments.
+int orc_reverse_flops(const orc_desc* d, int64_t N, int32_t T, const double* state0, const double* actions,
+                      int64_t* out, int32_t n_threads) {
+  System s = make_system(d);
+  const int B = s.B, A = s.A;
+  std::vector<int64_t> flops(N, 0), nodes(N, 0);
+  parallel_for(N, n_threads, [&](int64_t n) {
+    Tape tape;
+    tl_tape = &tape;
+    std::vector<Body<Var>> qp(B);
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < 13; ++i) *comp(qp[b], i) = var_leaf(state0[(n * B + b) * 13 + i]);
+    std::vector<Var> act(A > 0 ? A : 1);
+    for (int t = 0; t < T; ++t) {
+      for (int a = 0; a < A; ++a) act[a] = var_leaf(actions[((int64_t)t * N + n) * A + a]);
+      step(s, qp.data(), act.data(), (Diag*)nullptr);
+    }
+    flops[n] = 2 * tape.edges() + tape.deriv_flops;
+    nodes[n] = (int64_t)tape.nodes.size();
+    tl_tape = nullptr;
+  });
+  out[0] = out[1] = 0;
+  for (int64_t n = 0; n < N; ++n) {
+    out[0] += flops[n];
+    out[1] += nodes[n];
+  }
+  return 0;
+}
+
 // Forward-mode derivative (Jacobian-vector product) of a rollout along the
 // direction (d_state0 [N,B,13], d_actions [T,N,A]).  Outputs d_state_T
 // [N,B,13] and d_torso [T,N,3] (optional).

@@ -83,6 +83,15 @@ inline Dual atan2(Dual y, Dual x) {
 struct Tape {
   struct Node { int a, b; double da, db; };
   std::vector<Node> nodes;
+  // flops spent forming local partial derivatives (divide, sqrt, atan2) of
+  // recorded nodes; with 2 flops per edge of the reverse sweep this is the
+  // tape's reverse-op count
+  int64_t deriv_flops = 0;
+  int64_t edges() const {
+    int64_t e = 0;
+    for (const Node& n : nodes) e += (n.a >= 0) + (n.b >= 0);
+    return e;
+  }
   int push(int a, double da, int b, double db) {
     nodes.push_back(Node{a, b, da, db});
     return (int)nodes.size() - 1;
@@ -122,14 +131,17 @@ inline Var operator-(Var a, Var b) { return var_bin(a.v - b.v, a, 1.0, b, -1.0);
 inline Var operator*(Var a, Var b) { return var_bin(a.v * b.v, a, b.v, b, a.v); }
 inline Var operator/(Var a, Var b) {
   double q = a.v / b.v;
+  if (a.i >= 0 || b.i >= 0) tl_tape->deriv_flops += 2;
   return var_bin(q, a, 1.0 / b.v, b, -q / b.v);
 }
 inline Var operator-(Var a) { return var_un(-a.v, a, -1.0); }
 inline Var sqrt(Var a) {
   double s = std::sqrt(a.v);
+  if (a.i >= 0) tl_tape->deriv_flops += 1;
   return var_un(s, a, s > 0.0 ? 0.5 / s : 0.0);
 }
 inline Var atan2(Var y, Var x) {
+  if (y.i >= 0 || x.i >= 0) tl_tape->deriv_flops += 5;
   double r2 = x.v * x.v + y.v * y.v;
   double dy = r2 > 0.0 ? x.v / r2 : 0.0;
   double dx = r2 > 0.0 ? -y.v / r2 : 0.0;

@@ -577,3 +577,24 @@ def test_flop_counter_categories():
         assert counts[k] > 0
     # per-body work is per body and substep: 2 envs x 3 steps x 10 substeps x 9 bodies
     assert counts["body"] % (2 * 3 * 10 * 9) == 0
+
+
+def test_reverse_op_count_is_additive():
+    """The tape's reverse-op count (the reverse pass's algorithmic flops) adds
+    over environments and steps: two identical environments count twice one,
+    and a free body's steps (no contact, no joint) all cost the same."""
+    d = S.pendulum()
+    N = 2
+    rp, rr, ang = S.initial_conditions(d, 1, 5)
+    st1 = orc.default_qp(d, 1, rp, rr, ang)
+    a1 = S.actions(d, 1, 3, 5).astype(np.float64)
+    f1, n1 = orc.reverse_flops(d, st1, a1)
+    f2, n2 = orc.reverse_flops(d, np.repeat(st1, N, axis=0), np.repeat(a1, N, axis=1))
+    assert f2 == N * f1 and n2 == N * n1 and f1 > 0
+    sb = S.SceneBuilder()
+    sb.body("ball", 1.0, (0.4, 0.4, 0.4), (0, 0, 5.0))
+    free = sb.build()
+    st = orc.default_qp(free, 1, np.array([[0, 0, 5.0]]), None, None)
+    one, _ = orc.reverse_flops(free, st, np.zeros((1, 1, 0)))
+    three, _ = orc.reverse_flops(free, st, np.zeros((3, 1, 0)))
+    assert three == 3 * one
