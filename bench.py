@@ -506,7 +506,18 @@ def run_workload(args):
             batch.rollout_backward(st, a, o["checkpoints"], gT, T, K=K, workspace=ws)
 
         ms_f = _timed(fwd, args.warmup, steps)
-        ms = _timed(fb, args.warmup, steps)
+        # forward + reverse captured in one CUDA graph (two kernel nodes), replayed
+        for _ in range(2):
+            fb()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                fb()
+        torch.cuda.current_stream().wait_stream(side)
+        ms = _timed(graph.replay, args.warmup, steps)
         fl = sum(alg_flops(n)["flops_per_env_step"] * k for n, k in zip(names, ns)) / sum(ns)
         lines.append({"metric": "env-steps/s fwd+bwd, heterogeneous batch (one launch each way)",
                       "value": sum(ns) * T / ms * 1e3, "unit": "env-steps/s", "ms_per_step": ms, "steps": steps,
@@ -514,7 +525,7 @@ def run_workload(args):
                                    "roofline": roof(fl, sum(ns) * T, ms_f)},
                       "config": {"workload": "32768 pendulum + 16384 quadruped + 8192 biped + 8192 arm+box, "
                                              "200 steps, checkpoints every 10", "checkpoint_every": K},
-                      "tuning": {"warps_per_block": warps}})
+                      "tuning": {"warps_per_block": warps}, "cuda_graph": True})
     for ln in lines:
         ln.update({"n_gpus": 1, "warmup": args.warmup, "dtype": "f32", "data": "synthetic", "higher_is_better": True})
         print(json.dumps(ln), flush=True)

@@ -111,7 +111,10 @@ def test_batch_cuda_graph(batch_setup):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out["state_T"], eager["state_T"])
-    assert torch.equal(gs, e_gs) and torch.equal(ga, e_ga)
+    # the reverse pass sums body-body pair adjoints with shared-memory float
+    # atomics, whose order may differ between runs
+    rel = lambda x, y: ((x - y).norm() / y.norm()).item()
+    assert rel(gs, e_gs) < 1e-4 and rel(ga, e_ga) < 1e-4
 
 
 def test_batch_autotune_keeps_results(batch_setup):
