@@ -198,10 +198,10 @@ def run_ours(args):
         tuning.update(fwd_kernel="two_envs_per_thread" if r["fwd_kernel"] else "one_env_per_thread",
                       fwd_groups=r["fwd_groups"], fwd_variant=r["fwd_variant"], fwd_candidates=r["n_candidates"])
         if args.checkpoint_every <= 0:
-            nt = min(N, 16384)  # the reverse candidates are timed on a slice of the workload
-            rr_ = sysm.autotune(state0[:nt].contiguous(), actions[:, :nt].contiguous(), reverse=True, forward=False)
+            # (the reverse candidates are timed on the first 16384 environments)
+            rr_ = sysm.autotune(state0, actions, reverse=True, forward=False)
             K = rr_["K"]
-            tuning.update(K=K, bwd_variant=rr_["bwd_variant"], reverse_sample_envs=nt)
+            tuning.update(K=K, bwd_variant=rr_["bwd_variant"], reverse_sample_envs=min(N, 16384))
 
     def step():
         sysm.rollout(state0, actions, state_T=state_T)

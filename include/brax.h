@@ -225,10 +225,11 @@ int brax_sync_status(const brax_system* sys, void* stream);
  * returned in `out` (K is advice: the caller passes it to brax_rollout and
  * brax_rollout_backward).
  *   state0 [n_envs, B, 13], actions [T, n_envs, A]: device arrays of the
- *     workload (the forward is timed on min(T, 10) steps of it, the reverse
- *     on min(T, max(2 K, 20)) steps per candidate K);
- *   mem_budget: bytes the reverse candidates may hold (checkpoints +
- *     workspace); 0 = half of the free device memory.
+ *     workload (the forward is timed on min(T, 50) steps of it, the reverse
+ *     on min(T, max(2 K, 20)) steps of its first min(n_envs, 16384)
+ *     environments per candidate K);
+ *   mem_budget: bytes a candidate K may need for the whole (n_envs, T)
+ *     rollout (checkpoints + workspace); 0 = half of the free device memory.
  * Unlike the compute calls this one allocates temporary device memory and
  * synchronizes `stream`.  Returns BRAX_OK, or the first error of a call it
  * could not recover from. */

@@ -8,8 +8,9 @@
 // {1, 2, 4, 5, 8, 10, 16, 20, 25, 50, 100} (K <= T, checkpoints + workspace
 // within the memory budget) times the reverse kernel's launch-bounds
 // variants; the figure compared is (forward with checkpoints + reverse) per
-// step.  Each candidate runs once untimed, then twice timed with CUDA events;
-// the smaller time counts.
+// step, timed on the first min(n_envs, 16384) environments.  Each candidate
+// runs once untimed, then three times timed with CUDA events; the smallest
+// time counts.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,13 +35,13 @@ struct Events {
   }
 };
 
-// Runs fn (which returns a brax status) once untimed and twice timed on st.
-// Returns the smaller time in ms, or a negative value when fn failed.
+// Runs fn (which returns a brax status) once untimed and three times timed
+// on st.  Returns the smallest time in ms, or a negative value when fn failed.
 template <class F>
 float time_best(F fn, cudaStream_t st, Events& ev) {
   if (fn() != BRAX_OK) return -1.f;
   float best = -1.f;
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < 3; ++r) {
     cudaEventRecord(ev.a, st);
     if (fn() != BRAX_OK) return -1.f;
     cudaEventRecord(ev.b, st);
@@ -89,7 +90,7 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
   float* state_T = static_cast<float*>(stT.p);
 
   if (flags & BRAX_TUNE_FORWARD) {
-    const int Tf = std::min(T, 10);
+    const int Tf = std::min(T, 50);
     struct Cand {
       int kernel, groups, variant;
     };
@@ -136,33 +137,52 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
       mem_budget = fr / 2;
     }
     const int Ks[] = {1, 2, 4, 5, 8, 10, 16, 20, 25, 50, 100};
+    // candidates are timed on the first n_r environments over Tb steps; a K
+    // qualifies when its checkpoints and workspace for the full (n_envs, T)
+    // rollout fit the budget
+    const int64_t n_r = std::min<int64_t>(n_envs, 16384);
+    const size_t r_state_bytes = (size_t)n_r * s->B * 13 * sizeof(float);
     struct Plan {
       int K, Tb;
-      size_t ck_bytes, ws_bytes;
+      size_t ck_bytes, ws_bytes;  // of the timing sample
     };
     std::vector<Plan> plans;
     for (int K : Ks) {
       if (K > T) break;
       const int Tb = std::min(T, std::max(2 * K, 20));
-      size_t ws = 0;
-      if (brax_workspace_size(s, n_envs, Tb, K, &ws) != BRAX_OK) return BRAX_ERR_INVALID_ARGUMENT;
-      const size_t ck = (size_t)((Tb + K - 1) / K) * state_bytes;
-      if (ck + ws <= mem_budget) plans.push_back({K, Tb, ck, ws});
+      size_t ws_full = 0, ws_r = 0;
+      if (brax_workspace_size(s, n_envs, T, K, &ws_full) != BRAX_OK ||
+          brax_workspace_size(s, n_r, Tb, K, &ws_r) != BRAX_OK)
+        return BRAX_ERR_INVALID_ARGUMENT;
+      const size_t ck_full = (size_t)((T + K - 1) / K) * state_bytes;
+      if (ck_full + ws_full <= mem_budget) plans.push_back({K, Tb, (size_t)((Tb + K - 1) / K) * r_state_bytes, ws_r});
     }
     if (plans.empty()) return tune_fail(BRAX_ERR_OUT_OF_MEMORY, "brax_autotune: no checkpoint interval fits the budget");
     size_t ck_max = 0, ws_max = 0;
+    int Tb_max = 0;
     for (const Plan& p : plans) {
       ck_max = std::max(ck_max, p.ck_bytes);
       ws_max = std::max(ws_max, p.ws_bytes);
+      Tb_max = std::max(Tb_max, p.Tb);
     }
-    int Tb_max = 0;
-    for (const Plan& p : plans) Tb_max = std::max(Tb_max, p.Tb);
-    DeviceBuffer ck, ws, gst, gs0, gact;
-    const size_t act_bytes = (size_t)Tb_max * n_envs * std::max(s->A, 1) * sizeof(float);
-    if (ck.alloc(ck_max) != cudaSuccess || ws.alloc(ws_max) != cudaSuccess || gst.alloc(state_bytes) != cudaSuccess ||
-        gs0.alloc(state_bytes) != cudaSuccess || gact.alloc(act_bytes) != cudaSuccess)
+    DeviceBuffer ck, ws, gst, gs0, gact, sst, sact;
+    const size_t row = (size_t)n_r * std::max(s->A, 1) * sizeof(float);
+    if (ck.alloc(ck_max) != cudaSuccess || ws.alloc(ws_max) != cudaSuccess || gst.alloc(r_state_bytes) != cudaSuccess ||
+        gs0.alloc(r_state_bytes) != cudaSuccess || gact.alloc((size_t)Tb_max * row) != cudaSuccess)
       return tune_fail(BRAX_ERR_OUT_OF_MEMORY, "brax_autotune: cudaMalloc");
-    cudaMemsetAsync(gst.p, 0, state_bytes, st);
+    cudaMemsetAsync(gst.p, 0, r_state_bytes, st);
+    const float* r_state0 = state0;
+    const float* r_actions = actions;
+    if (n_r < n_envs) {  // copy out the sample's states and action rows
+      if (sst.alloc(r_state_bytes) != cudaSuccess || sact.alloc((size_t)Tb_max * row) != cudaSuccess)
+        return tune_fail(BRAX_ERR_OUT_OF_MEMORY, "brax_autotune: cudaMalloc");
+      cudaMemcpyAsync(sst.p, state0, r_state_bytes, cudaMemcpyDeviceToDevice, st);
+      if (s->A > 0)
+        cudaMemcpy2DAsync(sact.p, (size_t)n_r * s->A * sizeof(float), actions, (size_t)n_envs * s->A * sizeof(float),
+                          (size_t)n_r * s->A * sizeof(float), Tb_max, cudaMemcpyDeviceToDevice, st);
+      r_state0 = static_cast<const float*>(sst.p);
+      if (s->A > 0) r_actions = static_cast<const float*>(sact.p);
+    }
     const int threads = 32 * s->B;
     float best = -1.f;
     int bestK = plans[0].K, bestV = -1;
@@ -173,10 +193,10 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
         s->bwd_variant = v;
         const float ms = time_best(
             [&] {
-              int rc = brax_rollout(s, n_envs, p.Tb, p.K, state0, actions, state_T, static_cast<float*>(ck.p), nullptr,
-                                    nullptr, stream);
+              int rc = brax_rollout(s, n_r, p.Tb, p.K, r_state0, r_actions, state_T, static_cast<float*>(ck.p),
+                                    nullptr, nullptr, stream);
               if (rc == BRAX_OK)
-                rc = brax_rollout_backward(s, n_envs, p.Tb, p.K, state0, actions, static_cast<float*>(ck.p),
+                rc = brax_rollout_backward(s, n_r, p.Tb, p.K, r_state0, r_actions, static_cast<float*>(ck.p),
                                            static_cast<float*>(gst.p), nullptr, static_cast<float*>(gact.p),
                                            static_cast<float*>(gs0.p), ws.p, ws_max, stream);
               return rc;
