@@ -62,3 +62,25 @@ def test_autotune_applies_a_timed_configuration(brax, name, tmp_path):
     r2 = other.autotune(cuda(st), cuda(a), reverse=True, cache=cache)
     assert r2["cached"] and r2["K"] == r["K"] and r2["fwd_kernel"] == r["fwd_kernel"]
     assert r2["fwd_groups"] == r["fwd_groups"] and r2["fwd_variant"] == r["fwd_variant"]
+
+
+def test_autotune_respects_the_memory_budget(brax):
+    """A budget too small for any checkpoint interval of the whole rollout is
+    reported, not exceeded; a budget that admits only large K picks one of
+    those."""
+    from paper_2106_13281_gb300.binding import BraxError
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 1024, 40
+    rp, rr, ang = S.initial_conditions(d, N, 5, height_jitter=0.05)
+    st = cuda(orc.default_qp(d, N, rp, rr, ang))
+    a = cuda(S.actions(d, N, T, 6))
+    with pytest.raises(BraxError) as ei:
+        sysm.autotune(st, a, reverse=True, forward=False, mem_budget=1024)
+    assert ei.value.code == 4
+    state_bytes = N * sysm.B * 13 * 4
+    need = lambda K: -(-T // K) * state_bytes + sysm.workspace_size(N, T, K)
+    budget = need(10)  # admits K = 10; K = 1 and 2 need more
+    assert need(1) > budget and need(2) > budget
+    r = sysm.autotune(st, a, reverse=True, forward=False, mem_budget=budget)
+    assert r["K"] > 2 and need(r["K"]) <= budget
