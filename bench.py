@@ -53,6 +53,15 @@ def parse():
     return p.parse_args()
 
 
+def headline_config(N, T, substeps, dt, A, world):
+    """The workload both arms report (the reference arm times a bounded sample
+    of it, described in its cpu_baseline.sample)."""
+    return {"workload": f"quadruped-9body forward rollout, {N} envs x {T} steps x {substeps} substeps",
+            "envs": N, "steps_per_rollout": T, "substeps": substeps, "dt": dt,
+            "l2": "inputs larger than L2 (actions %.2f GB per rollout)" % (N * T * A * 4 / 1e9),
+            "parallelism": f"env shards x{world}"}
+
+
 def kernel_sources_digest():
     """sha256 over the CUDA sources (csrc/*.cu, *.cuh, *.h, sorted by name)."""
     import hashlib
@@ -311,10 +320,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded PCG64 actions uniform[-1,1], initial joint angles N(0,0.1^2), heights 0.75+U(0,0.05))",
-        "config": {"workload": "quadruped-9body forward rollout, 65536 envs x 1000 steps x 10 substeps",
-                   "envs": N, "steps_per_rollout": T, "substeps": int(d["substeps"]), "dt": float(d["dt"]),
-                   "l2": "inputs larger than L2 (actions %.2f GB per rollout)" % (actions.numel() * 4 / 1e9),
-                   "parallelism": f"env shards x{world}"},
+        "config": headline_config(N, T, int(d["substeps"]), float(d["dt"]), d["gear"].shape[0], world),
         "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "BraxSystem.rollout_streamed (pinned host inputs, %d-step chunks overlapped with compute)"
                        % e2e_chunk, "gpu_launches_per_step": math.ceil(T / e2e_chunk)},
@@ -394,8 +400,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "quadruped-9body forward rollout (bounded CPU sample)", "envs": n_envs,
-                   "steps_per_rollout": T},
+        "config": headline_config(args.envs, args.horizon, int(d["substeps"]), float(d["dt"]), d["gear"].shape[0],
+                                  args.gpus),
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
