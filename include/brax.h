@@ -153,7 +153,13 @@ int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, con
  *   checkpoints   [ceil(T/K), N, B, 13]: the state at steps 0, K, 2K, ... (the
  *                 input of brax_rollout_backward; K >= 1);
  *   torso_traj    [T, N, 3]: body 0's position after every step;
- *   contact_count [N] int32: active contacts summed over all substeps. */
+ *   contact_count [N] int32: active contacts summed over all substeps.
+ * Systems with hinge joints only and at most two plane-contact points per
+ * body run two environments per thread (packed FP32x2 arithmetic) when no
+ * checkpoints are requested; a rollout that writes checkpoints runs the
+ * one-environment kernel, whose arithmetic brax_rollout_backward recomputes
+ * with, so gradients do not depend on K.  The two kernels agree to FP32
+ * rounding. */
 int brax_rollout(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj,
                  int32_t* contact_count, void* stream);
