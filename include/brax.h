@@ -56,7 +56,7 @@ typedef enum {
   BRAX_ERR_CUDA = 3,               /* a CUDA call failed (message has the CUDA error) */
   BRAX_ERR_OUT_OF_MEMORY = 4,      /* allocation at create time failed */
   BRAX_ERR_NONFINITE = 5,          /* a kernel saw a non-finite state (brax_sync_status) */
-  BRAX_ERR_TIMEOUT = 6,            /* reserved: a bounded device wait gave up */
+  BRAX_ERR_TIMEOUT = 6,            /* a bounded device wait gave up (brax_sync_status) */
   BRAX_ERR_WORKSPACE = 7           /* workspace missing or smaller than brax_workspace_size */
 } brax_status;
 
@@ -159,7 +159,21 @@ int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, con
  * checkpoints are requested; a rollout that writes checkpoints runs the
  * one-environment kernel, whose arithmetic brax_rollout_backward recomputes
  * with, so gradients do not depend on K.  The two kernels agree to FP32
- * rounding. */
+ * rounding.
+ * Schedule of the two-environment kernel: a block keeps its environments on
+ * chip for the whole rollout, so when the blocks are not a whole number of
+ * resident waves the last wave would run part-empty from the first step to
+ * the last.  Then the rollout of each block of environments is cut into
+ * chunks of at least 16 steps, and resident blocks take (chunk, block) items
+ * in chunk-major order; a chunk continues from the state the previous one
+ * stored in state_T (so state_T must not overlap the actions, checkpoints or
+ * torso arrays) once a per-block flag says that chunk is done.  Results are
+ * bitwise those of the static schedule.  The flags and the item counter live
+ * in scratch the system owns (four regions used in turn by successive calls,
+ * so up to four rollouts of one system may overlap on the GPU); the first
+ * call that needs more of it allocates, and a call made while its stream is
+ * being captured that would need to allocate takes the static schedule.  A
+ * wait gives up after 2 s (brax_sync_status then reports BRAX_ERR_TIMEOUT). */
 int brax_rollout(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj,
                  int32_t* contact_count, void* stream);
@@ -218,8 +232,11 @@ int brax_batch_rollout_backward(const brax_batch* batch, int32_t T, int32_t K, c
                                 size_t workspace_bytes, void* stream);
 
 /* Synchronise `stream`, then read and clear the system's device status word:
- * BRAX_OK, or BRAX_ERR_NONFINITE if any kernel since the last call produced
- * a non-finite state.  Also reports a pending CUDA error as BRAX_ERR_CUDA. */
+ * BRAX_OK; BRAX_ERR_TIMEOUT if a chunk-scheduled rollout gave up waiting for
+ * the previous chunk of its environments (its outputs are then incomplete;
+ * see brax_rollout); else BRAX_ERR_NONFINITE if any kernel since the last
+ * call produced a non-finite state.  Also reports a pending CUDA error as
+ * BRAX_ERR_CUDA. */
 int brax_sync_status(const brax_system* sys, void* stream);
 
 /* ---------------------------------------------------------------- autotuner

@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH):
             L.brax_system_get_launch.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
             L.brax_system_get_pair_launch.argtypes = [P, C.POINTER(i32)]
             L.brax_system_set_backward_launch.argtypes = [P, i32]
+        if hasattr(L, "brax_system_set_schedule"):
+            L.brax_system_set_schedule.argtypes = [P, i32, i32, i32, i64]
         _lib = L
         return L
 

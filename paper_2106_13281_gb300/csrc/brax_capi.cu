@@ -545,6 +545,68 @@ Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
   return sg;
 }
 
+// Chunked schedule of a paired rollout of `units` blocks (Sched): taken when
+// the units leave the last resident wave less than 97 % full (mode 1) or
+// always (mode 2).  About 24 items per resident block keep the final
+// imbalance near one item; chunks of at least 16 steps keep the cost of a
+// chunk boundary (the state through L2, one flag wait) near 1 %.
+struct SchedPlan {
+  int n_chunks = 0, chunk_steps = 0, grid = 0;
+};
+SchedPlan plan_pair_schedule(const brax_system* s, int64_t units, int T, int threads, size_t smem) {
+  SchedPlan p;
+  if (s->sched_mode == 0 || T < 2 || units < 1) return p;
+  const int per_sm = pair_blocks_per_sm(s->pair_variant, threads, smem);
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+    cudaGetLastError();
+    return p;
+  }
+  const int64_t slots = (int64_t)per_sm * n_sm;
+  if (slots <= 0) return p;
+  int64_t chunk;
+  if (s->sched_mode == 2) {
+    chunk = std::max(1, s->sched_chunk);
+  } else {
+    const int64_t waves = (units + slots - 1) / slots;
+    if (units <= slots || (double)units >= 0.97 * (double)(waves * slots)) return p;
+    const int64_t want = (24 * slots + units - 1) / units;  // chunks per unit
+    chunk = std::max<int64_t>(16, (T + want - 1) / want);
+  }
+  const int64_t C = (T + chunk - 1) / chunk;
+  if (C < 2 || C * units > 0x3fffffff) return p;
+  p.n_chunks = (int)C;
+  p.chunk_steps = (int)chunk;
+  p.grid = (int)std::min<int64_t>(C * units, slots);
+  return p;
+}
+
+// One region of the scheduler scratch for a launch of `units` units (null
+// when it cannot be had: the caller then runs the static schedule).  Growing
+// the scratch allocates, which a stream under capture does not allow.
+int32_t* sched_region(const brax_system* s, int64_t units, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(s->sched_mu);
+  if (units > s->sched_units) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    const int64_t cap = std::max<int64_t>(units, 2 * s->sched_units);
+    int32_t* d = nullptr;
+    if (cudaMalloc(&d, brax_system::kSchedRing * (32 + cap) * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (s->d_sched) s->sched_retired.push_back(s->d_sched);
+    s->d_sched = d;
+    s->sched_units = cap;
+  }
+  const int r = s->sched_next;
+  s->sched_next = (r + 1) % brax_system::kSchedRing;
+  return s->d_sched + r * (32 + s->sched_units);
+}
+
 }  // namespace
 
 extern "C" {
@@ -609,6 +671,8 @@ void brax_system_destroy(brax_system* s) {
   if (s->pool_off >= 0) pool_release(s->device, s->pool_off);
   cudaFree(s->d_blob);
   cudaFree(s->d_status);
+  if (s->d_sched) cudaFree(s->d_sched);
+  for (int32_t* d : s->sched_retired) cudaFree(d);
   delete s;
 }
 
@@ -657,6 +721,15 @@ int brax_system_get_launch(const brax_system* s, int32_t* groups, int32_t* varia
   if (!s || !groups || !variant) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_get_launch: null argument");
   *groups = s->groups;
   *variant = s->variant;
+  return BRAX_OK;
+}
+int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item, int64_t wait_ns) {
+  if (!s || mode < 0 || mode > 2 || (mode == 2 && chunk_steps < 1) || first_item < 0 || wait_ns < 1)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_schedule: bad arguments");
+  s->sched_mode = mode;
+  s->sched_chunk = chunk_steps;
+  s->sched_first = first_item;
+  s->sched_wait_ns = wait_ns;
   return BRAX_OK;
 }
 int brax_system_get_pair_launch(const brax_system* s, int32_t* mode) {
@@ -712,8 +785,23 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     sg.ccount = contact_count;
     L.seg[0] = sg;
     const size_t smem = s->pair_groups * pair_group_bytes(s->B);
-    cudaError_t e = launch_rollout_pair(L, (int)grid, 32 * s->B * s->pair_groups, smem, s->pair_variant,
-                                        as_stream(stream));
+    const int threads = 32 * s->B * s->pair_groups;
+    int launch_grid = (int)grid;
+    const SchedPlan pl = plan_pair_schedule(s, grid, T, threads, smem);
+    if (pl.n_chunks > 0) {
+      if (int32_t* region = sched_region(s, grid, as_stream(stream))) {
+        cudaError_t e = cudaMemsetAsync(region, 0, (32 + grid) * sizeof(int32_t), as_stream(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "brax_rollout");
+        L.sc.n_chunks = pl.n_chunks;
+        L.sc.chunk_steps = pl.chunk_steps;
+        L.sc.n_units = (int32_t)grid;
+        L.sc.first_item = s->sched_first;
+        L.sc.sched = region;
+        L.sc.wait_ns = s->sched_wait_ns;
+        launch_grid = pl.grid;
+      }
+    }
+    cudaError_t e = launch_rollout_pair(L, launch_grid, threads, smem, s->pair_variant, as_stream(stream));
     return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
   }
   Seg sg = make_seg(s, s->groups, n_envs);
@@ -747,6 +835,9 @@ int brax_sync_status(const brax_system* s, void* stream) {
   e = cudaMemcpy(&h, s->d_status, sizeof(h), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && h) e = cudaMemset(s->d_status, 0, sizeof(int32_t));
   if (e != cudaSuccess) return cuda_fail(e, "brax_sync_status");
+  if (h & kStatusTimeout)
+    return fail(BRAX_ERR_TIMEOUT, "brax_sync_status: a rollout block gave up waiting for the previous chunk of its "
+                                  "environments (the rollout's outputs are incomplete)");
   if (h) return fail(BRAX_ERR_NONFINITE, "brax_sync_status: a kernel produced a non-finite state");
   return BRAX_OK;
 }

@@ -41,12 +41,54 @@ struct Seg {
   float* ws;  // per-segment workspace
 };
 
+// Chunked schedule of a persistent rollout (two-environments-per-thread
+// kernel).  A block's environments stay on chip for a whole rollout, so when
+// the blocks of a launch are not a whole number of resident waves the last
+// wave runs part-empty for the whole rollout.  Instead the rollout of each
+// block-sized unit of environments is cut into n_chunks chunks of chunk_steps
+// steps, and resident blocks take (chunk, unit) items from a counter in
+// chunk-major order; chunk c of a unit starts from the state that chunk c-1
+// left in state_T, after the flag of that unit says chunk c-1 is done.
+// sched[0] is the counter, sched[32 + u] the flag of unit u (chunks done);
+// both start at zero.  n_chunks = 0: one unit per block, the whole rollout.
+struct Sched {
+  int32_t n_chunks = 0;
+  int32_t chunk_steps = 0;
+  int32_t n_units = 0;
+  int32_t first_item = 0;     // first item the counter hands out (0 except in the wait test)
+  int32_t* sched = nullptr;
+  int64_t wait_ns = 0;        // a wait for a flag gives up after this long (BRAX_ERR_TIMEOUT)
+};
+
 struct Launch {
   int32_t n_segs;
   int32_t T, K;
   int32_t pad;
   Seg seg[BRAX_MAX_SEGS];
+  Sched sc;
 };
+
+// Status bits a kernel ORs into Seg::status (brax_sync_status reports them).
+constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
+
+// Wait until *flag >= v (acquire, GPU scope), sleeping between polls; false
+// when wait_ns nanoseconds of the global timer pass first.
+__device__ __forceinline__ bool wait_flag_at_least(const int32_t* flag, int32_t v, int64_t wait_ns) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    int32_t x;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(flag) : "memory");
+    if (x >= v) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((int64_t)(t - t0) > wait_ns) return false;
+    __nanosleep(200);
+  }
+}
+__device__ __forceinline__ void store_release(int32_t* p, int32_t v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ------------------------------------------------------------------ algebra
 struct V3 {

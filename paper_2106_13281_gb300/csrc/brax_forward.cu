@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
     bad |= !body_finite(s);
   }
   if (valid) store_body(sg.state_T + (env * B + b) * 13, s);
-  if (bad && valid) atomicOr(sg.status, 1);
+  if (bad && valid) atomicOr(sg.status, kStatusNonfinite);
   if (sg.ccount) {
     atomicAdd(&gm.cnt[lane], ccount);
     group_sync(bar, nthr);
@@ -169,7 +169,7 @@ namespace p2 {
 __device__ __forceinline__ void load_pair(const float* pa, const float* pb, const BodyP& bp, Body& s) {
   auto ld = [&](int i) {
     const float r = i < 3 ? bp.rest_pos[i] : (i < 7 ? bp.rest_rot[i - 3] : 0.f);
-    return make_float2(pa ? pa[i] : r, pb ? pb[i] : r);
+    return make_float2(pa ? __ldcg(pa + i) : r, pb ? __ldcg(pb + i) : r);
   };
   s.x = V{ld(0), ld(1), ld(2)};
   s.qw = ld(3);
@@ -182,19 +182,19 @@ __device__ __forceinline__ void load_pair(const float* pa, const float* pb, cons
 // Store one half (0: A, 1: B) of the pair state.
 __device__ __forceinline__ void store_half(float* p, const Body& s, int half) {
   auto h = [half](f2 v) { return half ? v.y : v.x; };
-  p[0] = h(s.x.x);
-  p[1] = h(s.x.y);
-  p[2] = h(s.x.z);
-  p[3] = h(s.qw);
-  p[4] = h(s.qx);
-  p[5] = h(s.qy);
-  p[6] = h(s.qz);
-  p[7] = h(s.v.x);
-  p[8] = h(s.v.y);
-  p[9] = h(s.v.z);
-  p[10] = h(s.w.x);
-  p[11] = h(s.w.y);
-  p[12] = h(s.w.z);
+  __stcg(p + 0, h(s.x.x));
+  __stcg(p + 1, h(s.x.y));
+  __stcg(p + 2, h(s.x.z));
+  __stcg(p + 3, h(s.qw));
+  __stcg(p + 4, h(s.qx));
+  __stcg(p + 5, h(s.qy));
+  __stcg(p + 6, h(s.qz));
+  __stcg(p + 7, h(s.v.x));
+  __stcg(p + 8, h(s.v.y));
+  __stcg(p + 9, h(s.v.z));
+  __stcg(p + 10, h(s.w.x));
+  __stcg(p + 11, h(s.w.y));
+  __stcg(p + 12, h(s.w.z));
 }
 __device__ __forceinline__ bool finite_pair(const Body& s) {
   const f2 t = add(add(add(s.x.x, s.x.y), add(s.x.z, s.qw)),
@@ -204,13 +204,15 @@ __device__ __forceinline__ bool finite_pair(const Body& s) {
 }  // namespace p2
 
 // Persistent rollout of a hinge-only system, two environments per thread
-// (brax_pair.cuh).  One launch segment; a block holds G groups of 64
-// environments.
+// (brax_pair.cuh).  A block holds G groups of 64 environments (a unit).
+// Without a chunked schedule block i runs unit i for the whole rollout; with
+// one (Sched) it runs the (chunk, unit) items it takes from the counter.
 template <int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_constant__ Launch L) {
   using namespace p2;
   const Seg& sg = L.seg[0];
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
   const unsigned char* blob = c_pool + sg.pool_off;
   const SysP& S = *reinterpret_cast<const SysP*>(blob);
   const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
@@ -222,82 +224,117 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
   const int g = warp / B, b = warp - g * B;
   if (g >= sg.groups) return;  // spare warps take no part in the group barriers
   const int64_t N = sg.n_envs;
-  const int64_t ea = ((int64_t)blockIdx.x * sg.groups + g) * 64 + lane, eb = ea + 32;
-  const bool va = ea < N, vb = eb < N;
   GroupMem2 gm = group_mem2(reinterpret_cast<float*>(smem) + g * group_floats2(B), B);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
   const BodyP2& q = bodies2[b];
-  if (b == 0) {
-    gm.cnt[lane] = 0;
-    gm.cnt[32 + lane] = 0;
-  }
-  if (sg.ccount) group_sync(bar, nthr);
-  p2::Body s;
-  load_pair(va ? sg.state0 + (ea * B + b) * 13 : nullptr, vb ? sg.state0 + (eb * B + b) * 13 : nullptr, bp, s);
   const int T = L.T, K = L.K, A = sg.A;
   const int nsub = S.substeps;
   const bool has_parent = (bp.flags & kHasParent) != 0, publishes = (bp.flags & kPublish) != 0;
   const int act_idx = bp.act[0];
   const int np = bp.n_points;
   const bool average = S.average != 0;
-  int cca = 0, ccb = 0;
-  bool bad = false;
-  for (int t = 0; t < T; ++t) {
-    if (sg.ckpt && (t % K) == 0) {
-      float* c = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
-      if (va) store_half(c + (ea * B + b) * 13, s, 0);
-      if (vb) store_half(c + (eb * B + b) * 13, s, 1);
-    }
-    f2 act = zero2();
-    if (has_parent && act_idx >= 0) {
-      const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
-      act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
-    }
-    for (int k = 0; k < nsub; ++k) {
-      kinematic(S2, bp.flags, s);
-      p2::Frame f;
-      f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
-      if (publishes) publish(gm, b, lane, s, f);
-      group_sync(bar, nthr);
-      if (has_parent) {
-        const p2::Pub pp = read_pub(gm, bp.parent, lane);
-        joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
+  const bool chunked = L.sc.n_chunks > 0;
+  const int n_units = L.sc.n_units, n_items = L.sc.n_chunks * n_units;
+  const int nblk = 32 * B * sg.groups;  // the threads of the block that take part
+  for (;;) {
+    int unit = blockIdx.x, c = 0, t0 = 0, t1 = T;
+    if (chunked) {
+      if (threadIdx.x == 0) {
+        int it = L.sc.first_item + atomicAdd(L.sc.sched, 1);
+        if (it < n_items && it >= n_units && !wait_flag_at_least(L.sc.sched + 32 + it % n_units, it / n_units,
+                                                                 L.sc.wait_ns)) {
+          atomicOr(sg.status, kStatusTimeout);
+          it = n_items;  // give up: this block takes no further item
+        }
+        s_item = it;
       }
-      p2::Acc acc{vzero(), vzero(), 0, 0};
-      f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
-      plane_points(S2, q, bp.flags, np, s, f, acc);
-      cca += acc.na;
-      ccb += acc.nb;
-      group_sync(bar, nthr);
-      integrate(S2, average, bp, q, gm, b, lane, s, f, acc);
+      group_sync(0, nblk);
+      const int it = s_item;  // rewritten only after the block barrier that ends the item
+      if (it >= n_items) break;
+      unit = it % n_units;
+      c = it / n_units;
+      t0 = c * L.sc.chunk_steps;
+      t1 = min(T, t0 + L.sc.chunk_steps);
     }
-    if (sg.torso && b == 0) {
-      float* tp = sg.torso + (int64_t)t * N * 3;
-      if (va) {
-        tp[ea * 3 + 0] = s.x.x.x;
-        tp[ea * 3 + 1] = s.x.y.x;
-        tp[ea * 3 + 2] = s.x.z.x;
-      }
-      if (vb) {
-        tp[eb * 3 + 0] = s.x.x.y;
-        tp[eb * 3 + 1] = s.x.y.y;
-        tp[eb * 3 + 2] = s.x.z.y;
-      }
-    }
-    bad |= !finite_pair(s);
-  }
-  if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
-  if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
-  if (bad && (va || vb)) atomicOr(sg.status, 1);
-  if (sg.ccount) {
-    atomicAdd(&gm.cnt[lane], cca);
-    atomicAdd(&gm.cnt[32 + lane], ccb);
-    group_sync(bar, nthr);
+    const int64_t ea = ((int64_t)unit * sg.groups + g) * 64 + lane, eb = ea + 32;
+    const bool va = ea < N, vb = eb < N;
     if (b == 0) {
-      if (va) sg.ccount[ea] = gm.cnt[lane];
-      if (vb) sg.ccount[eb] = gm.cnt[32 + lane];
+      gm.cnt[lane] = 0;
+      gm.cnt[32 + lane] = 0;
     }
+    if (sg.ccount) group_sync(bar, nthr);
+    p2::Body s;
+    {
+      // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
+      const float* src = c == 0 ? sg.state0 : sg.state_T;
+      load_pair(va ? src + (ea * B + b) * 13 : nullptr, vb ? src + (eb * B + b) * 13 : nullptr, bp, s);
+    }
+    int cca = 0, ccb = 0;
+    bool bad = false;
+    for (int t = t0; t < t1; ++t) {
+      if (sg.ckpt && (t % K) == 0) {
+        float* ck = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
+        if (va) store_half(ck + (ea * B + b) * 13, s, 0);
+        if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
+      }
+      f2 act = zero2();
+      if (has_parent && act_idx >= 0) {
+        const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
+        act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
+      }
+      for (int k = 0; k < nsub; ++k) {
+        kinematic(S2, bp.flags, s);
+        p2::Frame f;
+        f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
+        if (publishes) publish(gm, b, lane, s, f);
+        group_sync(bar, nthr);
+        if (has_parent) {
+          const p2::Pub pp = read_pub(gm, bp.parent, lane);
+          joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
+        }
+        p2::Acc acc{vzero(), vzero(), 0, 0};
+        f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
+        plane_points(S2, q, bp.flags, np, s, f, acc);
+        cca += acc.na;
+        ccb += acc.nb;
+        group_sync(bar, nthr);
+        integrate(S2, average, bp, q, gm, b, lane, s, f, acc);
+      }
+      if (sg.torso && b == 0) {
+        float* tp = sg.torso + (int64_t)t * N * 3;
+        if (va) {
+          tp[ea * 3 + 0] = s.x.x.x;
+          tp[ea * 3 + 1] = s.x.y.x;
+          tp[ea * 3 + 2] = s.x.z.x;
+        }
+        if (vb) {
+          tp[eb * 3 + 0] = s.x.x.y;
+          tp[eb * 3 + 1] = s.x.y.y;
+          tp[eb * 3 + 2] = s.x.z.y;
+        }
+      }
+      bad |= !finite_pair(s);
+    }
+    if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
+    if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
+    if (bad && (va || vb)) atomicOr(sg.status, kStatusNonfinite);
+    // (the item's chunk and unit are read again rather than kept live through the steps)
+    const int c_end = chunked ? s_item / n_units : 0;
+    if (sg.ccount) {
+      atomicAdd(&gm.cnt[lane], cca);
+      atomicAdd(&gm.cnt[32 + lane], ccb);
+      group_sync(bar, nthr);
+      if (b == 0) {
+        if (va) __stcg(sg.ccount + ea, (c_end ? __ldcg(sg.ccount + ea) : 0) + gm.cnt[lane]);
+        if (vb) __stcg(sg.ccount + eb, (c_end ? __ldcg(sg.ccount + eb) : 0) + gm.cnt[32 + lane]);
+      }
+    }
+    if (!chunked) break;
+    // the item is done: its stores are made visible, then the unit's flag says so
+    __threadfence();
+    group_sync(0, nblk);
+    if (threadIdx.x == 0) store_release(L.sc.sched + 32 + s_item % n_units, c_end + 1);
   }
 }
 
@@ -418,6 +455,22 @@ cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t s
     case 1: return launch_pair_t<576, 1>(L, grid, threads, smem, st);
     case 3: return launch_pair_t<288, 3>(L, grid, threads, smem, st);
     default: return launch_pair_t<1024, 1>(L, grid, threads, smem, st);
+  }
+}
+template <int MAXT, int MINB>
+static int pair_occupancy_t(int threads, size_t smem) {
+  auto k = rollout_pair_kernel<MAXT, MINB>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
+}
+int pair_blocks_per_sm(int variant, int threads, size_t smem) {
+  switch (variant) {
+    case 0: return pair_occupancy_t<288, 2>(threads, smem);
+    case 1: return pair_occupancy_t<576, 1>(threads, smem);
+    case 3: return pair_occupancy_t<288, 3>(threads, smem);
+    default: return pair_occupancy_t<1024, 1>(threads, smem);
   }
 }
 int pair_variant_max_threads(int variant) {

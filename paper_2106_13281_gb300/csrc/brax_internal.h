@@ -1,6 +1,9 @@
 // Host-side definition of a system handle (shared by the C ABI translation
 // units).
 #pragma once
+#include <stdint.h>
+
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -23,6 +26,22 @@ struct brax_system {
   int pair_groups = 1;   // groups of 64 environments per thread block
   int pair_variant = 0;  // launch-bounds variant of the paired kernel
   int bwd_variant = -1;  // launch-bounds variant of the reverse kernel (-1: smallest that fits)
+  // Chunked schedule of paired rollouts (Sched in brax_device.cuh).  Mode 1
+  // (default): used when the blocks do not fill a whole number of resident
+  // waves; 0: never; 2: always, with chunks of sched_chunk steps.
+  int sched_mode = 1;
+  int sched_chunk = 0;
+  int sched_first = 0;              // first item handed out (the wait test starts past chunk 0)
+  int64_t sched_wait_ns = 2000000000;
+  // Scheduler scratch: kSchedRing regions of (32 + sched_units) int32, taken
+  // in turn by successive launches so that rollouts on different streams do
+  // not share one; replaced buffers are freed with the system.
+  static constexpr int kSchedRing = 4;
+  mutable std::mutex sched_mu;
+  mutable int32_t* d_sched = nullptr;
+  mutable int64_t sched_units = 0;
+  mutable int sched_next = 0;
+  mutable std::vector<int32_t*> sched_retired;
 };
 
 struct brax_batch {
@@ -33,6 +52,11 @@ struct brax_batch {
 
 extern "C" int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant);
 extern "C" int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant);
+// Chunked schedule of paired rollouts: mode 0 off, 1 automatic, 2 always with
+// chunks of chunk_steps steps; first_item > 0 and a short wait_ns serve the
+// test of the bounded wait (items past chunk 0 wait for flags nothing sets).
+extern "C" int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item,
+                                        int64_t wait_ns);
 
 
 namespace brax {

@@ -19,6 +19,8 @@ int rollout_variant_max_threads(int variant);
 // Two environments per thread (systems whose blob carries the paired section).
 cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
 int pair_variant_max_threads(int variant);
+// Resident blocks per SM of a paired-kernel variant (0 if it cannot launch).
+int pair_blocks_per_sm(int variant, int threads, size_t smem);
 size_t pair_group_bytes(int B);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);

@@ -62,6 +62,14 @@ class BraxSystem:
         falls back to the one-environment kernel."""
         check(self._L.brax_system_set_pair_launch(self._h, mode, groups, variant))
 
+    def set_schedule(self, mode: int, chunk_steps: int = 0, first_item: int = 0, wait_ns: int = 2_000_000_000):
+        """Chunked schedule of paired rollouts (resident blocks take (chunk,
+        environment block) items so that the last wave is not part-empty):
+        mode 1 automatic (default), 0 never, 2 always with chunks of
+        chunk_steps steps.  first_item and wait_ns exist for the test of the
+        bounded wait."""
+        check(self._L.brax_system_set_schedule(self._h, mode, chunk_steps, first_item, wait_ns))
+
     # ---------------------------------------------------------------- autotuner
     def _desc_digest(self) -> str:
         h = hashlib.sha1()

@@ -224,6 +224,74 @@ def test_pair_kernel_matches_single_env_kernel(brax, name, drop):
     sysm.set_pair_launch(1, 1, 0)
 
 
+def _rollout_outputs(sysm, st, a):
+    out = sysm.rollout(st, a, torso=True, contact_count=True)
+    sysm.sync_status()
+    return out
+
+
+@pytest.mark.parametrize("N,T,chunk", [(37, 10, 3), (100, 7, 1), (1000, 12, 5)])
+def test_chunked_schedule_equals_static(brax, N, T, chunk):
+    """Chunked schedule of the paired rollout (blocks take (chunk,
+    environment block) items; a chunk starts from the state the previous one
+    left in memory): bitwise the static schedule's final state, torso
+    trajectory and contact counts, ragged tails and chunks that do not divide
+    T included."""
+    d = S.quadruped()
+    sysm = brax(d)
+    st, _ = initial(d, N, 21, drop=0.38)
+    st, a = cuda(st), cuda(S.actions(d, N, T, 22))
+    sysm.set_schedule(0)
+    ref = _rollout_outputs(sysm, st, a)
+    sysm.set_schedule(2, chunk)
+    got = _rollout_outputs(sysm, st, a)
+    sysm.set_schedule(1)
+    for k in ("state_T", "torso", "contact_count"):
+        assert torch.equal(got[k], ref[k]), k
+
+
+def test_automatic_schedule_at_several_waves(brax):
+    """40,000 environments are 625 blocks of 64, about two resident waves and
+    a part-empty third: the automatic schedule chunks the rollout and still
+    equals the static one bitwise."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 40000, 40
+    st, _ = initial(d, N, 23, drop=0.38)
+    st, a = cuda(st), cuda(S.actions(d, N, T, 24))
+    sysm.set_pair_launch(1, 1, 0)
+    sysm.set_schedule(0)
+    ref = _rollout_outputs(sysm, st, a)
+    sysm.set_schedule(1)
+    got = _rollout_outputs(sysm, st, a)
+    for k in ("state_T", "torso", "contact_count"):
+        assert torch.equal(got[k], ref[k]), k
+
+
+def test_schedule_wait_gives_up_with_timeout_status(brax):
+    """The bounded wait of the chunked schedule: when the counter starts past
+    chunk 0, every item waits for a flag that nothing sets; after 1 ms each
+    block gives up, the status reads BRAX_ERR_TIMEOUT (6), and the context
+    still runs the next rollout."""
+    from paper_2106_13281_gb300.binding import BraxError
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 100, 10
+    st, _ = initial(d, N, 25, drop=0.38)
+    st, a = cuda(st), cuda(S.actions(d, N, T, 26))
+    sysm.set_pair_launch(1, 1, 0)
+    units = (N + 63) // 64
+    sysm.set_schedule(2, 3, units, 1_000_000)
+    sysm.rollout(st, a)
+    with pytest.raises(BraxError) as ei:
+        sysm.sync_status()
+    assert ei.value.code == 6
+    sysm.set_schedule(1)
+    sysm.sync_status()  # the flag was cleared
+    sysm.rollout(st, a)
+    sysm.sync_status()
+
+
 def test_pair_launch_rejected_for_general_systems(brax):
     from paper_2106_13281_gb300.binding import BraxError
     sysm = brax(S.biped())
