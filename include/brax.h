@@ -160,20 +160,22 @@ int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, con
  * one-environment kernel, whose arithmetic brax_rollout_backward recomputes
  * with, so gradients do not depend on K.  The two kernels agree to FP32
  * rounding.
- * Schedule of the two-environment kernel: a block keeps its environments on
- * chip for the whole rollout, so when the blocks are not a whole number of
- * resident waves the last wave would run part-empty from the first step to
- * the last.  Then the rollout of each block of environments is cut into
- * chunks of at least 16 steps, and resident blocks take (chunk, block) items
- * in chunk-major order; a chunk continues from the state the previous one
- * stored in state_T (so state_T must not overlap the actions, checkpoints or
- * torso arrays) once a per-block flag says that chunk is done.  Results are
- * bitwise those of the static schedule.  The flags and the item counter live
- * in scratch the system owns (four regions used in turn by successive calls,
- * so up to four rollouts of one system may overlap on the GPU); the first
- * call that needs more of it allocates, and a call made while its stream is
- * being captured that would need to allocate takes the static schedule.  A
- * wait gives up after 2 s (brax_sync_status then reports BRAX_ERR_TIMEOUT). */
+ * Schedule: a block keeps its environments on chip for the whole rollout,
+ * so when the blocks are not a whole number of resident waves the last wave
+ * would run part-empty from the first step to the last.  Then the rollout of
+ * each block of environments is cut into chunks of at least 16 steps and the
+ * launch has one block per (chunk, block of environments) item; a starting
+ * block takes the next item in chunk-major order from a counter, and a chunk
+ * continues from the state the previous chunk stored in state_T (so state_T
+ * must not overlap the actions, checkpoints or torso arrays) once a
+ * per-block flag says that chunk is done.  Results are bitwise those of the
+ * static schedule.  The flags and the counter live in scratch the system
+ * owns (four regions used in turn by successive calls, so up to four
+ * rollouts of one system may overlap on the GPU); the first call that needs
+ * more of it allocates, and a call made while its stream is being captured
+ * that would need to allocate takes the static schedule.  A wait gives up
+ * after 2 s: the rollout stops, its outputs are incomplete and
+ * brax_sync_status reports BRAX_ERR_TIMEOUT. */
 int brax_rollout(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj,
                  int32_t* contact_count, void* stream);
@@ -223,6 +225,11 @@ void brax_batch_destroy(brax_batch* batch);
 /* Element offsets of system i's blocks in the concatenated arrays. */
 int brax_batch_offsets(const brax_batch* batch, int32_t T, int32_t K, int32_t i, int64_t* state_off,
                        int64_t* action_off, int64_t* torso_off, int64_t* ckpt_off);
+/* One launch over every system of the batch (brax_rollout's arguments, as
+ * concatenated blocks).  It takes the chunked schedule described at
+ * brax_rollout when the batch's blocks do not fill a whole number of resident
+ * waves (the scratch is the batch's; a wait that gives up is reported by the
+ * brax_sync_status of the system whose environments were waited for). */
 int brax_batch_rollout(const brax_batch* batch, int32_t T, int32_t K, const float* state0, const float* actions,
                        float* state_T, float* checkpoints, float* torso_traj, void* stream);
 int brax_batch_workspace_size(const brax_batch* batch, int32_t T, int32_t K, size_t* bytes);

@@ -114,6 +114,7 @@ def load_library(path: str = LIB_PATH):
             L.brax_system_set_backward_launch.argtypes = [P, i32]
         if hasattr(L, "brax_system_set_schedule"):
             L.brax_system_set_schedule.argtypes = [P, i32, i32, i32, i64]
+            L.brax_batch_set_schedule.argtypes = [P, i32, i32]
         _lib = L
         return L
 

@@ -42,8 +42,14 @@ __host__ __device__ inline int bwd_fwd_floats(int B, int P, bool slots_in_smem) 
   return B * kPubFields * 32 + B * kReactFields * 32 + (slots_in_smem ? P * kSlotFields * 32 : 0) + 32;
 }
 __host__ __device__ inline int bwd_group_floats(int B, int P) { return bwd_fwd_floats(B, P, false) + bwd_extra_floats(B, P); }
-__host__ __device__ inline int64_t ws_group_floats(int B, int P, int K, int S) {
+// Workspace of one group: step states [K][13][B][32], substep states
+// [S][13][B][32], pair slots [P][kSlotFields][32], and the state adjoint
+// carried from one chunk of a chunked schedule to the next [13][B][32].
+__host__ __device__ inline int64_t ws_carry_off(int B, int P, int K, int S) {
   return (int64_t)(K + S) * 13 * B * 32 + (int64_t)P * kSlotFields * 32;
+}
+__host__ __device__ inline int64_t ws_group_floats(int B, int P, int K, int S) {
+  return ws_carry_off(B, P, K, S) + (int64_t)13 * B * 32;
 }
 
 struct BwdMem {
@@ -286,12 +292,39 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);
 }
 
+// Reverse pass of a group of 32 environments: checkpoint segments last
+// first.  A block runs unit blockIdx.x over all segments or, under a chunked
+// schedule (Sched; chunk_steps counts segments, chunk 0 holds the last
+// ones), one chunk of the unit of the item it takes; the state adjoint then
+// passes from chunk to chunk through the workspace.
 template <int MAXT, int MINB, bool kGeneral>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_constant__ Launch L) {
-  int si = 0;
-  while (si + 1 < L.n_segs && (int)blockIdx.x >= L.seg[si].cta_end) ++si;
-  const Seg& sg = L.seg[si];
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const bool chunked = L.sc.n_chunks > 0;
+  int unit = blockIdx.x, c = 0;
+  if (chunked) {
+    const int n_units = L.sc.n_units, n_items = L.sc.n_chunks * n_units;
+    if (threadIdx.x == 0) {
+      int ticket;
+      const int it = take_item(L.sc, n_items, &ticket);
+      if (it == -2) {  // report the timeout to the system of the unit that was waited for
+        const int u = ticket % n_units;
+        int sj = 0;
+        while (sj + 1 < L.n_segs && u >= L.seg[sj].cta_end) ++sj;
+        atomicOr(L.seg[sj].status, kStatusTimeout);
+      }
+      s_item = it;
+    }
+    group_sync(0, blockDim.x);
+    const int it = s_item;
+    if (it < 0 || it >= n_items) return;
+    unit = it % n_units;
+    c = it / n_units;
+  }
+  int si = 0;
+  while (si + 1 < L.n_segs && unit >= L.seg[si].cta_end) ++si;
+  const Seg& sg = L.seg[si];
   const unsigned char* blob = c_pool + sg.pool_off;
   const SysP& S = *reinterpret_cast<const SysP*>(blob);
   const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
@@ -303,7 +336,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
   const int g = warp / B, b = warp - g * B;
   if (g >= sg.groups) return;
   const int64_t N = sg.n_envs;
-  const int64_t group = (int64_t)(blockIdx.x - sg.cta_begin) * sg.groups + g;
+  const int64_t group = (int64_t)(unit - sg.cta_begin) * sg.groups + g;
   const int64_t env = group * 32 + lane;
   const bool valid = env < N;
   float* gbase = reinterpret_cast<float*>(smem) + g * bwd_group_floats(B, P);
@@ -334,8 +367,24 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
 #pragma unroll
     for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
+  const int nseg = (T + K - 1) / K;
+  const int seg_hi = chunked ? nseg - c * L.sc.chunk_steps : nseg;
+  const int seg_lo = chunked ? max(0, seg_hi - L.sc.chunk_steps) : 0;
   GBody gs = zero_gbody();
-  if (valid) {
+  if (c > 0) {  // L2 loads: the previous chunk may have run on another SM
+    // the adjoint carried between chunks (lane-contiguous, like the step states)
+    const float* carry = ws_steps + ws_carry_off(B, P, K, nsub);
+    float v[13];
+#pragma unroll
+    for (int i = 0; i < 13; ++i) v[i] = __ldcg(carry + i * stride);
+    gs.x = mk3(v[0], v[1], v[2]);
+    gs.q[0] = v[3];
+    gs.q[1] = v[4];
+    gs.q[2] = v[5];
+    gs.q[3] = v[6];
+    gs.v = mk3(v[7], v[8], v[9]);
+    gs.w = mk3(v[10], v[11], v[12]);
+  } else if (valid) {
     const float* p = sg.g_state_T + (env * B + b) * 13;
     gs.x = mk3(p[0], p[1], p[2]);
     gs.q[0] = p[3];
@@ -346,7 +395,6 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
     gs.w = mk3(p[10], p[11], p[12]);
   }
   const int A = sg.A;
-  const int nseg = (T + K - 1) / K;
   float act[3] = {0.f, 0.f, 0.f};
   auto load_act = [&](int t) {
     if (valid && (bp.flags & kHasParent)) {
@@ -355,7 +403,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
       for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
     }
   };
-  for (int seg = nseg - 1; seg >= 0; --seg) {
+  for (int seg = seg_hi - 1; seg >= seg_lo; --seg) {
     const int t0 = seg * K, t1 = min(T, t0 + K);
     Body s;
     if (valid) {
@@ -405,7 +453,13 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
       }
     }
   }
-  if (valid && sg.g_state0) {
+  if (seg_lo > 0) {  // not the first segments yet: hand the adjoint to the next chunk
+    float* carry = ws_steps + ws_carry_off(B, P, K, nsub);
+    const float v[13] = {gs.x.x, gs.x.y, gs.x.z, gs.q[0], gs.q[1], gs.q[2], gs.q[3],
+                         gs.v.x, gs.v.y, gs.v.z, gs.w.x, gs.w.y, gs.w.z};
+#pragma unroll
+    for (int i = 0; i < 13; ++i) __stcg(carry + i * stride, v[i]);
+  } else if (valid && sg.g_state0) {
     float* p = sg.g_state0 + (env * B + b) * 13;
     p[0] = gs.x.x;
     p[1] = gs.x.y;
@@ -420,6 +474,36 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
     p[10] = gs.w.x;
     p[11] = gs.w.y;
     p[12] = gs.w.z;
+  }
+  if (chunked) {  // the item is done: its stores are made visible, then the unit's flag says so
+    __threadfence();
+    group_sync(0, 32 * B * sg.groups);
+    if (threadIdx.x == 0) store_release(L.sc.sched + 32 + unit, c + 1);
+  }
+}
+
+template <int MAXT, int MINB, bool G>
+static int bwd_occupancy_t(int threads, size_t smem) {
+  auto k = rollout_bwd_kernel<MAXT, MINB, G>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
+}
+int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem) {
+  if (general) {
+    switch (variant) {
+      case 0: return bwd_occupancy_t<384, 2, true>(threads, smem);
+      case 1: return bwd_occupancy_t<576, 1, true>(threads, smem);
+      case 3: return bwd_occupancy_t<288, 3, true>(threads, smem);
+      default: return bwd_occupancy_t<1024, 1, true>(threads, smem);
+    }
+  }
+  switch (variant) {
+    case 0: return bwd_occupancy_t<384, 2, false>(threads, smem);
+    case 1: return bwd_occupancy_t<576, 1, false>(threads, smem);
+    case 3: return bwd_occupancy_t<288, 3, false>(threads, smem);
+    default: return bwd_occupancy_t<1024, 1, false>(threads, smem);
   }
 }
 

@@ -545,66 +545,92 @@ Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
   return sg;
 }
 
-// Chunked schedule of a paired rollout of `units` blocks (Sched): taken when
-// the units leave the last resident wave less than 97 % full (mode 1) or
-// always (mode 2).  About 24 items per resident block keep the final
-// imbalance near one item; chunks of at least 16 steps keep the cost of a
-// chunk boundary (the state through L2, one flag wait) near 1 %.
+// Chunked schedule of a rollout of `units` blocks (Sched), per_sm of which
+// are resident per SM, over T steps (reverse pass: T checkpoint segments):
+// taken when the units leave the last resident wave less than 97 % full
+// (mode 1) or always (mode 2, chunks of `chunk` steps).  About 24 items per
+// resident block keep the final imbalance near one item; chunks of at least
+// min_chunk steps (16; in segments, 16 steps' worth) keep the cost of a chunk
+// boundary (the state through L2, a new block, one flag check) near 1 %.
 struct SchedPlan {
-  int n_chunks = 0, chunk_steps = 0, grid = 0;
+  int n_chunks = 0, chunk_steps = 0;
 };
-SchedPlan plan_pair_schedule(const brax_system* s, int64_t units, int T, int threads, size_t smem) {
+SchedPlan plan_schedule(int mode, int chunk, int device, int64_t units, int T, int per_sm, int min_chunk = 16) {
   SchedPlan p;
-  if (s->sched_mode == 0 || T < 2 || units < 1) return p;
-  const int per_sm = pair_blocks_per_sm(s->pair_variant, threads, smem);
+  if (mode == 0 || T < 2 || units < 1 || per_sm < 1) return p;
   int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     cudaGetLastError();
     return p;
   }
   const int64_t slots = (int64_t)per_sm * n_sm;
-  if (slots <= 0) return p;
-  int64_t chunk;
-  if (s->sched_mode == 2) {
-    chunk = std::max(1, s->sched_chunk);
+  int64_t steps;
+  if (mode == 2) {
+    steps = std::max(1, chunk);
   } else {
     const int64_t waves = (units + slots - 1) / slots;
     if (units <= slots || (double)units >= 0.97 * (double)(waves * slots)) return p;
     const int64_t want = (24 * slots + units - 1) / units;  // chunks per unit
-    chunk = std::max<int64_t>(16, (T + want - 1) / want);
+    steps = std::max<int64_t>(min_chunk, (T + want - 1) / want);
   }
-  const int64_t C = (T + chunk - 1) / chunk;
+  const int64_t C = (T + steps - 1) / steps;
   if (C < 2 || C * units > 0x3fffffff) return p;
   p.n_chunks = (int)C;
-  p.chunk_steps = (int)chunk;
-  p.grid = (int)std::min<int64_t>(C * units, slots);
+  p.chunk_steps = (int)steps;
   return p;
 }
 
-// One region of the scheduler scratch for a launch of `units` units (null
-// when it cannot be had: the caller then runs the static schedule).  Growing
-// the scratch allocates, which a stream under capture does not allow.
-int32_t* sched_region(const brax_system* s, int64_t units, cudaStream_t st) {
-  std::lock_guard<std::mutex> lk(s->sched_mu);
-  if (units > s->sched_units) {
+// One region of a scheduler scratch for a launch of `units` units (null when
+// it cannot be had: the caller then runs the static schedule).  Growing the
+// scratch allocates, which a stream under capture does not allow.
+int32_t* sched_region(SchedScratch& sc, int64_t units, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(sc.mu);
+  if (units > sc.units) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
       cudaGetLastError();
       return nullptr;
     }
-    const int64_t cap = std::max<int64_t>(units, 2 * s->sched_units);
+    const int64_t cap = std::max<int64_t>(units, 2 * sc.units);
     int32_t* d = nullptr;
-    if (cudaMalloc(&d, brax_system::kSchedRing * (32 + cap) * sizeof(int32_t)) != cudaSuccess) {
+    if (cudaMalloc(&d, SchedScratch::kRing * (32 + cap) * sizeof(int32_t)) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    if (s->d_sched) s->sched_retired.push_back(s->d_sched);
-    s->d_sched = d;
-    s->sched_units = cap;
+    if (sc.d) sc.retired.push_back(sc.d);
+    sc.d = d;
+    sc.units = cap;
   }
-  const int r = s->sched_next;
-  s->sched_next = (r + 1) % brax_system::kSchedRing;
-  return s->d_sched + r * (32 + s->sched_units);
+  const int r = sc.next;
+  sc.next = (r + 1) % SchedScratch::kRing;
+  return sc.d + r * (32 + sc.units);
+}
+void sched_free(SchedScratch& sc) {
+  if (sc.d) cudaFree(sc.d);
+  for (int32_t* d : sc.retired) cudaFree(d);
+  sc.d = nullptr;
+  sc.retired.clear();
+}
+
+// Fill L.sc for a chunked launch of `units` units when the plan asks for one
+// and scratch can be had; returns the grid (one block per item, or `units`).
+// Fails only if zeroing the scratch region fails.
+cudaError_t apply_schedule(const SchedPlan& pl, SchedScratch& sc, int first_item, int64_t wait_ns, int64_t units,
+                           Launch& L, int64_t* grid, cudaStream_t st) {
+  *grid = units;
+  if (pl.n_chunks == 0) return cudaSuccess;
+  int32_t* region = sched_region(sc, units, st);
+  if (!region) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(region, 0, (32 + units) * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  L.sc.n_chunks = pl.n_chunks;
+  L.sc.chunk_steps = pl.chunk_steps;
+  L.sc.n_units = (int32_t)units;
+  L.sc.first_item = first_item;
+  L.sc.sched = region;
+  L.sc.wait_ns = wait_ns;
+  *grid = (int64_t)pl.n_chunks * units;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -671,8 +697,7 @@ void brax_system_destroy(brax_system* s) {
   if (s->pool_off >= 0) pool_release(s->device, s->pool_off);
   cudaFree(s->d_blob);
   cudaFree(s->d_status);
-  if (s->d_sched) cudaFree(s->d_sched);
-  for (int32_t* d : s->sched_retired) cudaFree(d);
+  sched_free(s->sched);
   delete s;
 }
 
@@ -786,22 +811,13 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     L.seg[0] = sg;
     const size_t smem = s->pair_groups * pair_group_bytes(s->B);
     const int threads = 32 * s->B * s->pair_groups;
-    int launch_grid = (int)grid;
-    const SchedPlan pl = plan_pair_schedule(s, grid, T, threads, smem);
-    if (pl.n_chunks > 0) {
-      if (int32_t* region = sched_region(s, grid, as_stream(stream))) {
-        cudaError_t e = cudaMemsetAsync(region, 0, (32 + grid) * sizeof(int32_t), as_stream(stream));
-        if (e != cudaSuccess) return cuda_fail(e, "brax_rollout");
-        L.sc.n_chunks = pl.n_chunks;
-        L.sc.chunk_steps = pl.chunk_steps;
-        L.sc.n_units = (int32_t)grid;
-        L.sc.first_item = s->sched_first;
-        L.sc.sched = region;
-        L.sc.wait_ns = s->sched_wait_ns;
-        launch_grid = pl.grid;
-      }
-    }
-    cudaError_t e = launch_rollout_pair(L, launch_grid, threads, smem, s->pair_variant, as_stream(stream));
+    const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, T,
+                                       pair_blocks_per_sm(s->pair_variant, threads, smem));
+    int64_t launch_grid;
+    cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
+                                   as_stream(stream));
+    if (e == cudaSuccess)
+      e = launch_rollout_pair(L, (int)launch_grid, threads, smem, s->pair_variant, as_stream(stream));
     return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
   }
   Seg sg = make_seg(s, s->groups, n_envs);
@@ -818,7 +834,13 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   sg.ccount = contact_count;
   L.seg[0] = sg;
   const size_t smem = s->groups * group_bytes(s);
-  cudaError_t e = launch_rollout(L, (int)grid, 32 * s->B * s->groups, smem, s->variant, s->general, as_stream(stream));
+  const int threads = 32 * s->B * s->groups;
+  const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, T,
+                                     rollout_blocks_per_sm(s->variant, s->general, threads, smem));
+  int64_t launch_grid;
+  cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
+                                 as_stream(stream));
+  if (e == cudaSuccess) e = launch_rollout(L, (int)launch_grid, threads, smem, s->variant, s->general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
 }
 
@@ -874,7 +896,19 @@ int brax_batch_create(const brax_system* const* systems, const int64_t* n_envs, 
   return BRAX_OK;
 }
 
-void brax_batch_destroy(brax_batch* b) { delete b; }
+int brax_batch_set_schedule(brax_batch* b, int32_t mode, int32_t chunk_steps) {
+  if (!b || mode < 0 || mode > 2 || (mode == 2 && chunk_steps < 1))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_set_schedule: bad arguments");
+  b->sched_mode = mode;
+  b->sched_chunk = chunk_steps;
+  return BRAX_OK;
+}
+
+void brax_batch_destroy(brax_batch* b) {
+  if (!b) return;
+  sched_free(b->sched);
+  delete b;
+}
 
 int brax_batch_offsets(const brax_batch* b, int32_t T, int32_t K, int32_t i, int64_t* state_off, int64_t* action_off,
                        int64_t* torso_off, int64_t* ckpt_off) {
@@ -951,7 +985,13 @@ extern "C" int brax_batch_rollout(const brax_batch* b, int32_t T, int32_t K, con
   if (grid == 0) return BRAX_OK;
   const int variant = pick_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout: block too large");
-  cudaError_t e = launch_rollout(L, grid, threads, smem, variant, general, as_stream(stream));
+  int device = 0;
+  cudaGetDevice(&device);
+  const SchedPlan pl = plan_schedule(b->sched_mode, b->sched_chunk, device, grid, T,
+                                     rollout_blocks_per_sm(variant, general, threads, smem));
+  int64_t launch_grid;
+  cudaError_t e = apply_schedule(pl, b->sched, 0, 2000000000LL, grid, L, &launch_grid, as_stream(stream));
+  if (e == cudaSuccess) e = launch_rollout(L, (int)launch_grid, threads, smem, variant, general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout");
 }
 
@@ -1029,7 +1069,12 @@ extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32
       (s->bwd_variant >= 0 && threads <= rollout_variant_max_threads(s->bwd_variant)) ? s->bwd_variant : pick_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: system too large for one block");
   const size_t smem = backward_smem_bytes(s->B, s->P, 1);
-  cudaError_t e = launch_rollout_backward(L, (int)grid, threads, smem, variant, s->general, st);
+  const int nseg = (T + K - 1) / K;
+  const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, nseg,
+                                     backward_blocks_per_sm(variant, s->general, threads, smem), (16 + K - 1) / K);
+  int64_t launch_grid;
+  cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid, st);
+  if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, threads, smem, variant, s->general, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_backward");
 }
 
@@ -1120,6 +1165,12 @@ extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32
   }
   const int variant = pick_variant(pl.threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: block too large");
-  cudaError_t e = launch_rollout_backward(L, pl.grid, pl.threads, pl.smem, variant, pl.general, st);
+  int device = 0;
+  cudaGetDevice(&device);
+  const SchedPlan sp = plan_schedule(b->sched_mode, b->sched_chunk, device, pl.grid, (T + K - 1) / K,
+                                     backward_blocks_per_sm(variant, pl.general, pl.threads, pl.smem), (16 + K - 1) / K);
+  int64_t launch_grid;
+  cudaError_t e = apply_schedule(sp, b->sched, 0, 2000000000LL, pl.grid, L, &launch_grid, st);
+  if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, pl.threads, pl.smem, variant, pl.general, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout_backward");
 }

@@ -41,16 +41,20 @@ struct Seg {
   float* ws;  // per-segment workspace
 };
 
-// Chunked schedule of a persistent rollout (two-environments-per-thread
-// kernel).  A block's environments stay on chip for a whole rollout, so when
-// the blocks of a launch are not a whole number of resident waves the last
-// wave runs part-empty for the whole rollout.  Instead the rollout of each
-// block-sized unit of environments is cut into n_chunks chunks of chunk_steps
-// steps, and resident blocks take (chunk, unit) items from a counter in
-// chunk-major order; chunk c of a unit starts from the state that chunk c-1
-// left in state_T, after the flag of that unit says chunk c-1 is done.
-// sched[0] is the counter, sched[32 + u] the flag of unit u (chunks done);
-// both start at zero.  n_chunks = 0: one unit per block, the whole rollout.
+// Chunked schedule of a persistent rollout.  A block keeps its environments
+// on chip for the whole rollout, so when the blocks of a launch are not a
+// whole number of resident waves the last wave runs part-empty from the first
+// step to the last.  Instead the rollout of each block-sized unit of
+// environments is cut into n_chunks chunks of chunk_steps steps: the launch
+// has one block per (chunk, unit) item, and a block takes its item from a
+// counter when it starts, so items run in the order blocks start, chunk-major;
+// chunk c of a unit continues from the state that chunk c-1 left in state_T,
+// once the unit's flag says chunk c-1 is done.  A block that holds item i
+// started after the blocks holding items < i, so every wait ends.
+// sched[0] is the counter, sched[1] an abort flag (set by a block whose wait
+// gave up, so that later blocks stop at once), sched[32 + u] the flag of unit
+// u (chunks done); all start at zero.  n_chunks = 0: block i runs unit i for
+// the whole rollout.
 struct Sched {
   int32_t n_chunks = 0;
   int32_t chunk_steps = 0;
@@ -71,23 +75,40 @@ struct Launch {
 // Status bits a kernel ORs into Seg::status (brax_sync_status reports them).
 constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
 
-// Wait until *flag >= v (acquire, GPU scope), sleeping between polls; false
-// when wait_ns nanoseconds of the global timer pass first.
-__device__ __forceinline__ bool wait_flag_at_least(const int32_t* flag, int32_t v, int64_t wait_ns) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    int32_t x;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(flag) : "memory");
-    if (x >= v) return true;
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if ((int64_t)(t - t0) > wait_ns) return false;
-    __nanosleep(200);
-  }
+__device__ __forceinline__ int32_t load_acquire(const int32_t* p) {
+  int32_t x;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+  return x;
 }
 __device__ __forceinline__ void store_release(int32_t* p, int32_t v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0's part of starting a block under a chunked schedule: take the
+// block's item (the next ticket of the counter) and wait until the unit's
+// previous chunk is done.  Returns the item; n_items when there is none for
+// this block; -1 when the schedule was aborted; -2 when this wait gave up
+// after wait_ns nanoseconds of the global timer (it then sets the abort flag;
+// the caller reports kStatusTimeout).  *ticket is the ticket taken.
+__device__ __forceinline__ int take_item(const Sched& sc, int n_items, int* ticket) {
+  const int it = sc.first_item + atomicAdd(sc.sched, 1);
+  *ticket = it;
+  if (it >= n_items) return n_items;
+  if (it < sc.n_units) return it;  // chunk 0 waits for nothing
+  const int32_t* flag = sc.sched + 32 + it % sc.n_units;
+  const int32_t need = it / sc.n_units;
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (load_acquire(flag) >= need) return it;
+    if (load_acquire(sc.sched + 1) != 0) return -1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((int64_t)(t - t0) > sc.wait_ns) {
+      atomicExch(sc.sched + 1, 1);
+      return -2;
+    }
+    __nanosleep(200);
+  }
 }
 
 // ------------------------------------------------------------------ algebra

@@ -83,13 +83,40 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
 
 // Persistent rollout.  Parameters are read from the constant pool with a
 // warp-uniform body index (broadcast from lane 0 so the compiler can treat it
-// as uniform); the state stays in registers for all T x substeps.
+// as uniform); the state stays in registers for all T x substeps.  A block
+// runs one unit (a block-sized set of environment groups of one segment):
+// unit blockIdx.x for the whole rollout, or, under a chunked schedule
+// (Sched), one chunk of the unit of the item it takes.
 template <int MAXT, int MINB, bool kGeneral>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_constant__ Launch L) {
-  int si = 0;
-  while (si + 1 < L.n_segs && (int)blockIdx.x >= L.seg[si].cta_end) ++si;
-  const Seg& sg = L.seg[si];
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const bool chunked = L.sc.n_chunks > 0;
+  int unit = blockIdx.x, c = 0, t0 = 0, t1 = L.T;
+  if (chunked) {
+    const int n_units = L.sc.n_units, n_items = L.sc.n_chunks * n_units;
+    if (threadIdx.x == 0) {
+      int ticket;
+      const int it = take_item(L.sc, n_items, &ticket);
+      if (it == -2) {  // report the timeout to the system of the unit that was waited for
+        const int u = ticket % n_units;
+        int si = 0;
+        while (si + 1 < L.n_segs && u >= L.seg[si].cta_end) ++si;
+        atomicOr(L.seg[si].status, kStatusTimeout);
+      }
+      s_item = it;
+    }
+    group_sync(0, blockDim.x);
+    const int it = s_item;
+    if (it < 0 || it >= n_items) return;
+    unit = it % n_units;
+    c = it / n_units;
+    t0 = c * L.sc.chunk_steps;
+    t1 = min(L.T, t0 + L.sc.chunk_steps);
+  }
+  int si = 0;
+  while (si + 1 < L.n_segs && unit >= L.seg[si].cta_end) ++si;
+  const Seg& sg = L.seg[si];
   const unsigned char* blob = c_pool + sg.pool_off;
   const SysP& S = *reinterpret_cast<const SysP*>(blob);
   const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
@@ -101,7 +128,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   const int g = warp / B, b = warp - g * B;
   if (g >= sg.groups) return;  // spare warps take no part in the group barriers
   const int64_t N = sg.n_envs;
-  const int64_t env = ((int64_t)(blockIdx.x - sg.cta_begin) * sg.groups + g) * 32 + lane;
+  const int64_t env = ((int64_t)(unit - sg.cta_begin) * sg.groups + g) * 32 + lane;
   const bool valid = env < N;
   GroupMem gm = group_mem(reinterpret_cast<float*>(smem) + g * group_floats(B, sg.P), B, sg.P);
   const int bar = 1 + g, nthr = 32 * B;
@@ -112,8 +139,8 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   if (sg.ccount) group_sync(bar, nthr);
 
   Body s;
-  if (valid) {
-    load_body(sg.state0 + (env * B + b) * 13, s);
+  if (valid) {  // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
+    load_body_l2((c == 0 ? sg.state0 : sg.state_T) + (env * B + b) * 13, s);
   } else {  // padding lanes step a resting body and write nothing
     s.x = ld3(bp.rest_pos);
     s.qw = bp.rest_rot[0];
@@ -123,7 +150,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
     s.v = mk3(0.f, 0.f, 0.f);
     s.w = mk3(0.f, 0.f, 0.f);
   }
-  const int T = L.T, K = L.K, A = sg.A;
+  const int K = L.K, A = sg.A;
   const int nsub = S.substeps;
   int ccount = 0;
   bool bad = false;
@@ -135,7 +162,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
     if (bp.n_points > 0) pr[0] = point_regs(bp.pt[0]);
     if (bp.n_points > 1) pr[1] = point_regs(bp.pt[1]);
   }
-  for (int t = 0; t < T; ++t) {
+  for (int t = t0; t < t1; ++t) {
     if (sg.ckpt && valid && (t % K) == 0) store_body(sg.ckpt + (((int64_t)(t / K) * N + env) * B + b) * 13, s);
     if (valid && (bp.flags & kHasParent)) {
       const float* ap = sg.actions + ((int64_t)t * N + env) * A;
@@ -158,7 +185,12 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
   if (sg.ccount) {
     atomicAdd(&gm.cnt[lane], ccount);
     group_sync(bar, nthr);
-    if (b == 0 && valid) sg.ccount[env] = gm.cnt[lane];
+    if (b == 0 && valid) __stcg(sg.ccount + env, (c ? __ldcg(sg.ccount + env) : 0) + gm.cnt[lane]);
+  }
+  if (chunked) {  // the item is done: its stores are made visible, then the unit's flag says so
+    __threadfence();
+    group_sync(0, 32 * B * sg.groups);
+    if (threadIdx.x == 0) store_release(L.sc.sched + 32 + unit, c + 1);
   }
 }
 
@@ -182,19 +214,19 @@ __device__ __forceinline__ void load_pair(const float* pa, const float* pb, cons
 // Store one half (0: A, 1: B) of the pair state.
 __device__ __forceinline__ void store_half(float* p, const Body& s, int half) {
   auto h = [half](f2 v) { return half ? v.y : v.x; };
-  __stcg(p + 0, h(s.x.x));
-  __stcg(p + 1, h(s.x.y));
-  __stcg(p + 2, h(s.x.z));
-  __stcg(p + 3, h(s.qw));
-  __stcg(p + 4, h(s.qx));
-  __stcg(p + 5, h(s.qy));
-  __stcg(p + 6, h(s.qz));
-  __stcg(p + 7, h(s.v.x));
-  __stcg(p + 8, h(s.v.y));
-  __stcg(p + 9, h(s.v.z));
-  __stcg(p + 10, h(s.w.x));
-  __stcg(p + 11, h(s.w.y));
-  __stcg(p + 12, h(s.w.z));
+  p[0] = h(s.x.x);
+  p[1] = h(s.x.y);
+  p[2] = h(s.x.z);
+  p[3] = h(s.qw);
+  p[4] = h(s.qx);
+  p[5] = h(s.qy);
+  p[6] = h(s.qz);
+  p[7] = h(s.v.x);
+  p[8] = h(s.v.y);
+  p[9] = h(s.v.z);
+  p[10] = h(s.w.x);
+  p[11] = h(s.w.y);
+  p[12] = h(s.w.z);
 }
 __device__ __forceinline__ bool finite_pair(const Body& s) {
   const f2 t = add(add(add(s.x.x, s.x.y), add(s.x.z, s.qw)),
@@ -204,15 +236,33 @@ __device__ __forceinline__ bool finite_pair(const Body& s) {
 }  // namespace p2
 
 // Persistent rollout of a hinge-only system, two environments per thread
-// (brax_pair.cuh).  A block holds G groups of 64 environments (a unit).
-// Without a chunked schedule block i runs unit i for the whole rollout; with
-// one (Sched) it runs the (chunk, unit) items it takes from the counter.
+// (brax_pair.cuh).  A block holds G groups of 64 environments (a unit): unit
+// blockIdx.x for the whole rollout, or, under a chunked schedule (Sched), one
+// chunk of the unit of the item it takes.
 template <int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_constant__ Launch L) {
   using namespace p2;
   const Seg& sg = L.seg[0];
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
+  const bool chunked = L.sc.n_chunks > 0;
+  int unit = blockIdx.x, c = 0, t0 = 0, t1 = L.T;
+  if (chunked) {
+    const int n_units = L.sc.n_units, n_items = L.sc.n_chunks * n_units;
+    if (threadIdx.x == 0) {
+      int ticket;
+      const int it = take_item(L.sc, n_items, &ticket);
+      if (it == -2) atomicOr(sg.status, kStatusTimeout);
+      s_item = it;
+    }
+    group_sync(0, blockDim.x);
+    const int it = s_item;
+    if (it < 0 || it >= n_items) return;
+    unit = it % n_units;
+    c = it / n_units;
+    t0 = c * L.sc.chunk_steps;
+    t1 = min(L.T, t0 + L.sc.chunk_steps);
+  }
   const unsigned char* blob = c_pool + sg.pool_off;
   const SysP& S = *reinterpret_cast<const SysP*>(blob);
   const BodyP* bodies = reinterpret_cast<const BodyP*>(blob + blob_bodies_off());
@@ -224,117 +274,90 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
   const int g = warp / B, b = warp - g * B;
   if (g >= sg.groups) return;  // spare warps take no part in the group barriers
   const int64_t N = sg.n_envs;
+  const int64_t ea = ((int64_t)unit * sg.groups + g) * 64 + lane, eb = ea + 32;
+  const bool va = ea < N, vb = eb < N;
   GroupMem2 gm = group_mem2(reinterpret_cast<float*>(smem) + g * group_floats2(B), B);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
   const BodyP2& q = bodies2[b];
-  const int T = L.T, K = L.K, A = sg.A;
+  if (b == 0) {
+    gm.cnt[lane] = 0;
+    gm.cnt[32 + lane] = 0;
+  }
+  if (sg.ccount) group_sync(bar, nthr);
+  p2::Body s;
+  {  // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
+    const float* src = c == 0 ? sg.state0 : sg.state_T;
+    load_pair(va ? src + (ea * B + b) * 13 : nullptr, vb ? src + (eb * B + b) * 13 : nullptr, bp, s);
+  }
+  const int K = L.K, A = sg.A;
   const int nsub = S.substeps;
   const bool has_parent = (bp.flags & kHasParent) != 0, publishes = (bp.flags & kPublish) != 0;
   const int act_idx = bp.act[0];
   const int np = bp.n_points;
   const bool average = S.average != 0;
-  const bool chunked = L.sc.n_chunks > 0;
-  const int n_units = L.sc.n_units, n_items = L.sc.n_chunks * n_units;
-  const int nblk = 32 * B * sg.groups;  // the threads of the block that take part
-  for (;;) {
-    int unit = blockIdx.x, c = 0, t0 = 0, t1 = T;
-    if (chunked) {
-      if (threadIdx.x == 0) {
-        int it = L.sc.first_item + atomicAdd(L.sc.sched, 1);
-        if (it < n_items && it >= n_units && !wait_flag_at_least(L.sc.sched + 32 + it % n_units, it / n_units,
-                                                                 L.sc.wait_ns)) {
-          atomicOr(sg.status, kStatusTimeout);
-          it = n_items;  // give up: this block takes no further item
-        }
-        s_item = it;
-      }
-      group_sync(0, nblk);
-      const int it = s_item;  // rewritten only after the block barrier that ends the item
-      if (it >= n_items) break;
-      unit = it % n_units;
-      c = it / n_units;
-      t0 = c * L.sc.chunk_steps;
-      t1 = min(T, t0 + L.sc.chunk_steps);
+  int cca = 0, ccb = 0;
+  bool bad = false;
+  for (int t = t0; t < t1; ++t) {
+    if (sg.ckpt && (t % K) == 0) {
+      float* ck = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
+      if (va) store_half(ck + (ea * B + b) * 13, s, 0);
+      if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
     }
-    const int64_t ea = ((int64_t)unit * sg.groups + g) * 64 + lane, eb = ea + 32;
-    const bool va = ea < N, vb = eb < N;
-    if (b == 0) {
-      gm.cnt[lane] = 0;
-      gm.cnt[32 + lane] = 0;
+    f2 act = zero2();
+    if (has_parent && act_idx >= 0) {
+      const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
+      act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
     }
-    if (sg.ccount) group_sync(bar, nthr);
-    p2::Body s;
-    {
-      // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
-      const float* src = c == 0 ? sg.state0 : sg.state_T;
-      load_pair(va ? src + (ea * B + b) * 13 : nullptr, vb ? src + (eb * B + b) * 13 : nullptr, bp, s);
-    }
-    int cca = 0, ccb = 0;
-    bool bad = false;
-    for (int t = t0; t < t1; ++t) {
-      if (sg.ckpt && (t % K) == 0) {
-        float* ck = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
-        if (va) store_half(ck + (ea * B + b) * 13, s, 0);
-        if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
-      }
-      f2 act = zero2();
-      if (has_parent && act_idx >= 0) {
-        const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
-        act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
-      }
-      for (int k = 0; k < nsub; ++k) {
-        kinematic(S2, bp.flags, s);
-        p2::Frame f;
-        f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
-        if (publishes) publish(gm, b, lane, s, f);
-        group_sync(bar, nthr);
-        if (has_parent) {
-          const p2::Pub pp = read_pub(gm, bp.parent, lane);
-          joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
-        }
-        p2::Acc acc{vzero(), vzero(), 0, 0};
-        f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
-        plane_points(S2, q, bp.flags, np, s, f, acc);
-        cca += acc.na;
-        ccb += acc.nb;
-        group_sync(bar, nthr);
-        integrate(S2, average, bp, q, gm, b, lane, s, f, acc);
-      }
-      if (sg.torso && b == 0) {
-        float* tp = sg.torso + (int64_t)t * N * 3;
-        if (va) {
-          tp[ea * 3 + 0] = s.x.x.x;
-          tp[ea * 3 + 1] = s.x.y.x;
-          tp[ea * 3 + 2] = s.x.z.x;
-        }
-        if (vb) {
-          tp[eb * 3 + 0] = s.x.x.y;
-          tp[eb * 3 + 1] = s.x.y.y;
-          tp[eb * 3 + 2] = s.x.z.y;
-        }
-      }
-      bad |= !finite_pair(s);
-    }
-    if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
-    if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
-    if (bad && (va || vb)) atomicOr(sg.status, kStatusNonfinite);
-    // (the item's chunk and unit are read again rather than kept live through the steps)
-    const int c_end = chunked ? s_item / n_units : 0;
-    if (sg.ccount) {
-      atomicAdd(&gm.cnt[lane], cca);
-      atomicAdd(&gm.cnt[32 + lane], ccb);
+    for (int k = 0; k < nsub; ++k) {
+      kinematic(S2, bp.flags, s);
+      p2::Frame f;
+      f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
+      if (publishes) publish(gm, b, lane, s, f);
       group_sync(bar, nthr);
-      if (b == 0) {
-        if (va) __stcg(sg.ccount + ea, (c_end ? __ldcg(sg.ccount + ea) : 0) + gm.cnt[lane]);
-        if (vb) __stcg(sg.ccount + eb, (c_end ? __ldcg(sg.ccount + eb) : 0) + gm.cnt[32 + lane]);
+      if (has_parent) {
+        const p2::Pub pp = read_pub(gm, bp.parent, lane);
+        joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
+      }
+      p2::Acc acc{vzero(), vzero(), 0, 0};
+      f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
+      plane_points(S2, q, bp.flags, np, s, f, acc);
+      cca += acc.na;
+      ccb += acc.nb;
+      group_sync(bar, nthr);
+      integrate(S2, average, bp, q, gm, b, lane, s, f, acc);
+    }
+    if (sg.torso && b == 0) {
+      float* tp = sg.torso + (int64_t)t * N * 3;
+      if (va) {
+        tp[ea * 3 + 0] = s.x.x.x;
+        tp[ea * 3 + 1] = s.x.y.x;
+        tp[ea * 3 + 2] = s.x.z.x;
+      }
+      if (vb) {
+        tp[eb * 3 + 0] = s.x.x.y;
+        tp[eb * 3 + 1] = s.x.y.y;
+        tp[eb * 3 + 2] = s.x.z.y;
       }
     }
-    if (!chunked) break;
-    // the item is done: its stores are made visible, then the unit's flag says so
+    bad |= !finite_pair(s);
+  }
+  if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
+  if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
+  if (bad && (va || vb)) atomicOr(sg.status, kStatusNonfinite);
+  if (sg.ccount) {
+    atomicAdd(&gm.cnt[lane], cca);
+    atomicAdd(&gm.cnt[32 + lane], ccb);
+    group_sync(bar, nthr);
+    if (b == 0) {
+      if (va) __stcg(sg.ccount + ea, (c ? __ldcg(sg.ccount + ea) : 0) + gm.cnt[lane]);
+      if (vb) __stcg(sg.ccount + eb, (c ? __ldcg(sg.ccount + eb) : 0) + gm.cnt[32 + lane]);
+    }
+  }
+  if (chunked) {  // the item is done: its stores are made visible, then the unit's flag says so
     __threadfence();
-    group_sync(0, nblk);
-    if (threadIdx.x == 0) store_release(L.sc.sched + 32 + s_item % n_units, c_end + 1);
+    group_sync(0, 32 * B * sg.groups);
+    if (threadIdx.x == 0) store_release(L.sc.sched + 32 + unit, c + 1);
   }
 }
 
@@ -436,6 +459,31 @@ cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, 
     case 1: return launch_rollout_t<576, 1, false>(L, grid, threads, smem, st);
     case 3: return launch_rollout_t<288, 3, false>(L, grid, threads, smem, st);
     default: return launch_rollout_t<1024, 1, false>(L, grid, threads, smem, st);
+  }
+}
+
+template <int MAXT, int MINB, bool kGeneral>
+static int rollout_occupancy_t(int threads, size_t smem) {
+  auto k = rollout_kernel<MAXT, MINB, kGeneral>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
+}
+int rollout_blocks_per_sm(int variant, bool general, int threads, size_t smem) {
+  if (general) {
+    switch (variant) {
+      case 0: return rollout_occupancy_t<384, 2, true>(threads, smem);
+      case 1: return rollout_occupancy_t<576, 1, true>(threads, smem);
+      case 3: return rollout_occupancy_t<288, 3, true>(threads, smem);
+      default: return rollout_occupancy_t<1024, 1, true>(threads, smem);
+    }
+  }
+  switch (variant) {
+    case 0: return rollout_occupancy_t<384, 2, false>(threads, smem);
+    case 1: return rollout_occupancy_t<576, 1, false>(threads, smem);
+    case 3: return rollout_occupancy_t<288, 3, false>(threads, smem);
+    default: return rollout_occupancy_t<1024, 1, false>(threads, smem);
   }
 }
 

@@ -9,6 +9,20 @@
 
 #include "../../include/brax.h"
 
+namespace brax {
+// Scheduler scratch of chunked rollouts: kRing regions of (32 + units) int32,
+// taken in turn by successive launches so that rollouts on different streams
+// do not share one; replaced buffers are freed with the owner.
+struct SchedScratch {
+  static constexpr int kRing = 4;
+  std::mutex mu;
+  int32_t* d = nullptr;
+  int64_t units = 0;
+  int next = 0;
+  std::vector<int32_t*> retired;
+};
+}  // namespace brax
+
 struct brax_system {
   int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
   bool general = false;  // 3-DOF joints or body-body pairs present
@@ -26,35 +40,30 @@ struct brax_system {
   int pair_groups = 1;   // groups of 64 environments per thread block
   int pair_variant = 0;  // launch-bounds variant of the paired kernel
   int bwd_variant = -1;  // launch-bounds variant of the reverse kernel (-1: smallest that fits)
-  // Chunked schedule of paired rollouts (Sched in brax_device.cuh).  Mode 1
+  // Chunked schedule of rollouts (Sched in brax_device.cuh).  Mode 1
   // (default): used when the blocks do not fill a whole number of resident
   // waves; 0: never; 2: always, with chunks of sched_chunk steps.
   int sched_mode = 1;
   int sched_chunk = 0;
   int sched_first = 0;              // first item handed out (the wait test starts past chunk 0)
   int64_t sched_wait_ns = 2000000000;
-  // Scheduler scratch: kSchedRing regions of (32 + sched_units) int32, taken
-  // in turn by successive launches so that rollouts on different streams do
-  // not share one; replaced buffers are freed with the system.
-  static constexpr int kSchedRing = 4;
-  mutable std::mutex sched_mu;
-  mutable int32_t* d_sched = nullptr;
-  mutable int64_t sched_units = 0;
-  mutable int sched_next = 0;
-  mutable std::vector<int32_t*> sched_retired;
+  mutable brax::SchedScratch sched;
 };
 
 struct brax_batch {
   std::vector<const brax_system*> sys;
   std::vector<int64_t> n_envs;
   int warps = 0;  // warps per thread block
+  int sched_mode = 1, sched_chunk = 0;  // as brax_system's
+  mutable brax::SchedScratch sched;     // chunked schedule of the batch's forward rollouts
 };
 
 extern "C" int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant);
 extern "C" int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant);
-// Chunked schedule of paired rollouts: mode 0 off, 1 automatic, 2 always with
-// chunks of chunk_steps steps; first_item > 0 and a short wait_ns serve the
-// test of the bounded wait (items past chunk 0 wait for flags nothing sets).
+// Chunked schedule of a system's rollouts: mode 0 off, 1 automatic, 2 always
+// with chunks of chunk_steps steps; first_item > 0 and a short wait_ns serve
+// the test of the bounded wait (items past chunk 0 wait for flags nothing sets).
+extern "C" int brax_batch_set_schedule(brax_batch* b, int32_t mode, int32_t chunk_steps);
 extern "C" int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item,
                                         int64_t wait_ns);
 

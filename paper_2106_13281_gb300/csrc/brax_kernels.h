@@ -16,6 +16,8 @@ cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, 
 cudaError_t upload_pool_forward(int off, const void* data, size_t bytes);
 cudaError_t upload_pool_backward(int off, const void* data, size_t bytes);
 int rollout_variant_max_threads(int variant);
+// Resident blocks per SM of a one-environment kernel variant (0 if it cannot launch).
+int rollout_blocks_per_sm(int variant, bool general, int threads, size_t smem);
 // Two environments per thread (systems whose blob carries the paired section).
 cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
 int pair_variant_max_threads(int variant);
@@ -25,6 +27,8 @@ size_t pair_group_bytes(int B);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);
 size_t backward_smem_bytes(int B, int P, int groups);
+// Resident blocks per SM of a reverse kernel variant (0 if it cannot launch).
+int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem);
 int64_t backward_ws_floats_per_group(int B, int P, int K, int S);
 cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
                               const float* angles, float* out, cudaStream_t st);

@@ -48,6 +48,18 @@ __device__ __forceinline__ void load_body(const float* p, Body& s) {
   s.v = mk3(p[7], p[8], p[9]);
   s.w = mk3(p[10], p[11], p[12]);
 }
+// The same through L2 only: a chunk of a chunked rollout schedule starts from
+// a state that a block on another SM stored, which this SM's L1 may hold an
+// older copy of.
+__device__ __forceinline__ void load_body_l2(const float* p, Body& s) {
+  s.x = mk3(__ldcg(p + 0), __ldcg(p + 1), __ldcg(p + 2));
+  s.qw = __ldcg(p + 3);
+  s.qx = __ldcg(p + 4);
+  s.qy = __ldcg(p + 5);
+  s.qz = __ldcg(p + 6);
+  s.v = mk3(__ldcg(p + 7), __ldcg(p + 8), __ldcg(p + 9));
+  s.w = mk3(__ldcg(p + 10), __ldcg(p + 11), __ldcg(p + 12));
+}
 __device__ __forceinline__ void store_body(float* p, const Body& s) {
   p[0] = s.x.x;
   p[1] = s.x.y;

@@ -290,6 +290,11 @@ class BraxBatch:
             self._L.brax_batch_destroy(h)
             self._h = None
 
+    def set_schedule(self, mode: int, chunk_steps: int = 0):
+        """Chunked schedule of the batch's forward rollouts (as
+        BraxSystem.set_schedule): 1 automatic (default), 0 never, 2 always."""
+        check(self._L.brax_batch_set_schedule(self._h, mode, chunk_steps))
+
     def sizes(self, T, K=1):
         """Total elements of the state, action, torso and checkpoint arrays."""
         st = sum(n * s.B * 13 for s, n in zip(self.systems, self.n_envs))

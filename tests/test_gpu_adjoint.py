@@ -190,6 +190,73 @@ def test_checkpoint_interval_does_not_change_gradients(brax):
             assert np.array_equal(ga, ref[0]) and np.array_equal(gs, ref[1])
 
 
+@pytest.mark.parametrize("K,chunk", [(1, 3), (2, 2), (4, 1)])
+def test_chunked_schedule_reverse_equals_static(brax, K, chunk):
+    """The reverse pass under the chunked schedule (chunks of `chunk`
+    checkpoint segments, last first; the state adjoint passes between chunks
+    through the workspace), and the checkpointed forward under it: bitwise
+    the static schedule's gradients."""
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T = 45, 13
+    st = settled(d, N, 35, 0.38)
+    a = S.actions(d, N, T, 36)
+    rng = np.random.default_rng(37)
+    gT = rng.normal(size=st.shape)
+    gtor = rng.normal(size=(T, N, 3))
+    sysm.set_schedule(0)
+    ref = gpu_grad(sysm, st, a, gT, gtor, K)
+    sysm.set_schedule(2, chunk)
+    got = gpu_grad(sysm, st, a, gT, gtor, K)
+    sysm.set_schedule(1)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_chunked_schedule_reverse_general_kernel(brax):
+    """The same for the biped (3-DOF joints, capsule pairs): its pair
+    adjoints are summed with shared-memory atomics in no fixed order, so the
+    gradients agree to rounding (relative norm 1e-4) rather than bitwise."""
+    d = S.biped()
+    sysm = brax(d)
+    N, T, K = 40, 6, 1
+    st = settled(d, N, 38, 0.0)
+    a = S.actions(d, N, T, 39)
+    gT = np.random.default_rng(40).normal(size=st.shape)
+    sysm.set_schedule(0)
+    ref = gpu_grad(sysm, st, a, gT, None, K)
+    sysm.set_schedule(2, 2)
+    got = gpu_grad(sysm, st, a, gT, None, K)
+    sysm.set_schedule(1)
+    for x, y in zip(got[:2], ref[:2]):
+        assert np.linalg.norm(x - y) <= 1e-4 * np.linalg.norm(y)
+
+
+def test_reverse_schedule_wait_gives_up_with_timeout_status(brax):
+    """The reverse pass's bounded wait: with the counter started past chunk
+    0 every item waits for a flag nothing sets; the status reads
+    BRAX_ERR_TIMEOUT (6) and the next reverse pass runs normally."""
+    from paper_2106_13281_gb300.binding import BraxError
+    d = S.quadruped()
+    sysm = brax(d)
+    N, T, K = 70, 8, 1
+    st = settled(d, N, 41, 0.38)
+    a = S.actions(d, N, T, 42)
+    gT = np.random.default_rng(43).normal(size=st.shape)
+    units = (N + 31) // 32
+    sysm.set_schedule(0)
+    out = sysm.rollout(cuda(st), cuda(a), K=K, checkpoints=True)
+    sysm.set_schedule(2, 2, units, 1_000_000)
+    sysm.rollout_backward(cuda(st), cuda(a), out["checkpoints"], cuda(gT), None, K=K)
+    with pytest.raises(BraxError) as ei:
+        sysm.sync_status()
+    assert ei.value.code == 6
+    sysm.set_schedule(1)
+    sysm.sync_status()
+    ga, gs = sysm.rollout_backward(cuda(st), cuda(a), out["checkpoints"], cuda(gT), None, K=K)
+    sysm.sync_status()
+    assert torch.isfinite(ga).all() and torch.isfinite(gs).all()
+
+
 def test_long_rollout_gradients_finite(brax):
     """1000 steps with checkpoints every 10: the recomputation path runs and
     the gradients stay finite."""

@@ -66,6 +66,23 @@ def test_batch_forward_matches_solo(batch_setup):
         s.sync_status()
 
 
+def test_batch_chunked_schedule_equals_static(batch_setup):
+    """The batch forward under the chunked schedule (items of different
+    systems in one counter order): bitwise the static schedule."""
+    descs, systems, n_envs, batch = batch_setup
+    T, K = 9, 2
+    states, acts = make_inputs(descs, n_envs, T, 75)
+    outs = []
+    for mode, chunk in ((0, 0), (2, 2)):
+        batch.set_schedule(mode, chunk)
+        outs.append(batch.rollout(cat(states), cat(acts), T, K=K, checkpoints=True, torso=True))
+        for s in systems:
+            s.sync_status()
+    batch.set_schedule(1)
+    for k in ("state_T", "checkpoints", "torso"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+
+
 def test_batch_backward_matches_solo(batch_setup):
     descs, systems, n_envs, batch = batch_setup
     T, K = 5, 2

@@ -268,7 +268,29 @@ def test_automatic_schedule_at_several_waves(brax):
         assert torch.equal(got[k], ref[k]), k
 
 
-def test_schedule_wait_gives_up_with_timeout_status(brax):
+@pytest.mark.parametrize("name,drop", [("quadruped", 0.38), ("biped", 0.0)])
+def test_chunked_schedule_one_env_kernel(brax, name, drop):
+    """The one-environment kernel (rollouts with checkpoints; every system
+    with 3-DOF joints or body-body pairs) under the chunked schedule:
+    bitwise the static schedule's final state, checkpoints (K not dividing
+    the chunk), torso trajectory and contact counts."""
+    d = S.SCENES[name]()
+    sysm = brax(d)
+    N, T, K = 77, 11, 3
+    st, _ = initial(d, N, 27, drop=drop)
+    st, a = cuda(st), cuda(S.actions(d, N, T, 28))
+    outs = []
+    for mode, chunk in ((0, 0), (2, 4)):
+        sysm.set_schedule(mode, chunk)
+        outs.append(sysm.rollout(st, a, K=K, checkpoints=True, torso=True, contact_count=True))
+        sysm.sync_status()
+    sysm.set_schedule(1)
+    for k in ("state_T", "checkpoints", "torso", "contact_count"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("checkpoints", [False, True])
+def test_schedule_wait_gives_up_with_timeout_status(brax, checkpoints):
     """The bounded wait of the chunked schedule: when the counter starts past
     chunk 0, every item waits for a flag that nothing sets; after 1 ms each
     block gives up, the status reads BRAX_ERR_TIMEOUT (6), and the context
@@ -281,14 +303,16 @@ def test_schedule_wait_gives_up_with_timeout_status(brax):
     st, a = cuda(st), cuda(S.actions(d, N, T, 26))
     sysm.set_pair_launch(1, 1, 0)
     units = (N + 63) // 64
+    if checkpoints:  # the one-environment kernel: blocks of 32 environments
+        units = (N + 31) // 32
     sysm.set_schedule(2, 3, units, 1_000_000)
-    sysm.rollout(st, a)
+    sysm.rollout(st, a, checkpoints=checkpoints)
     with pytest.raises(BraxError) as ei:
         sysm.sync_status()
     assert ei.value.code == 6
     sysm.set_schedule(1)
     sysm.sync_status()  # the flag was cleared
-    sysm.rollout(st, a)
+    sysm.rollout(st, a, checkpoints=checkpoints)
     sysm.sync_status()
 
 
