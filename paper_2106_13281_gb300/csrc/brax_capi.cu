@@ -555,15 +555,10 @@ Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
 struct SchedPlan {
   int n_chunks = 0, chunk_steps = 0;
 };
-SchedPlan plan_schedule(int mode, int chunk, int device, int64_t units, int T, int per_sm, int min_chunk = 16) {
+// The plan for `slots` resident blocks (host arithmetic only).
+SchedPlan plan_schedule_slots(int mode, int chunk, int64_t units, int T, int64_t slots, int min_chunk) {
   SchedPlan p;
-  if (mode == 0 || T < 2 || units < 1 || per_sm < 1) return p;
-  int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-    cudaGetLastError();
-    return p;
-  }
-  const int64_t slots = (int64_t)per_sm * n_sm;
+  if (mode == 0 || T < 2 || units < 1 || slots < 1) return p;
   int64_t steps;
   if (mode == 2) {
     steps = std::max(1, chunk);
@@ -578,6 +573,15 @@ SchedPlan plan_schedule(int mode, int chunk, int device, int64_t units, int T, i
   p.n_chunks = (int)C;
   p.chunk_steps = (int)steps;
   return p;
+}
+SchedPlan plan_schedule(int mode, int chunk, int device, int64_t units, int T, int per_sm, int min_chunk = 16) {
+  if (mode == 0 || T < 2 || units < 1 || per_sm < 1) return SchedPlan{};
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return SchedPlan{};
+  }
+  return plan_schedule_slots(mode, chunk, units, T, (int64_t)per_sm * n_sm, min_chunk);
 }
 
 // One region of a scheduler scratch for a launch of `units` units (null when
@@ -746,6 +750,14 @@ int brax_system_get_launch(const brax_system* s, int32_t* groups, int32_t* varia
   if (!s || !groups || !variant) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_get_launch: null argument");
   *groups = s->groups;
   *variant = s->variant;
+  return BRAX_OK;
+}
+int brax_internal_plan_schedule(int32_t mode, int32_t chunk_steps, int64_t units, int32_t T, int64_t slots,
+                                int32_t min_chunk, int32_t* n_chunks, int32_t* steps) {
+  if (!n_chunks || !steps) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_internal_plan_schedule: null argument");
+  const SchedPlan p = plan_schedule_slots(mode, chunk_steps, units, T, slots, min_chunk);
+  *n_chunks = p.n_chunks;
+  *steps = p.chunk_steps;
   return BRAX_OK;
 }
 int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item, int64_t wait_ns) {

@@ -64,6 +64,10 @@ extern "C" int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t
 // with chunks of chunk_steps steps; first_item > 0 and a short wait_ns serve
 // the test of the bounded wait (items past chunk 0 wait for flags nothing sets).
 extern "C" int brax_batch_set_schedule(brax_batch* b, int32_t mode, int32_t chunk_steps);
+// The chunked-schedule plan for `slots` resident blocks (host arithmetic
+// only, for tests): n_chunks = 0 means the static schedule.
+extern "C" int brax_internal_plan_schedule(int32_t mode, int32_t chunk_steps, int64_t units, int32_t T, int64_t slots,
+                                           int32_t min_chunk, int32_t* n_chunks, int32_t* steps);
 extern "C" int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item,
                                         int64_t wait_ns);
 

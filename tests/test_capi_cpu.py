@@ -74,3 +74,42 @@ def test_null_arguments(lib):
     assert lib.brax_rollout(None, 1, 1, 1, None, None, None, None, None, None, None) == 1
     assert lib.brax_workspace_size(None, 1, 1, 1, None) == 1
     assert lib.brax_sync_status(None, None) == 1
+
+
+def plan(lib, mode, chunk, units, T, slots, min_chunk=16):
+    f = lib.brax_internal_plan_schedule
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int64, C.c_int32,
+                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    n, s = C.c_int32(), C.c_int32()
+    assert f(mode, chunk, units, T, slots, min_chunk, C.byref(n), C.byref(s)) == 0
+    return n.value, s.value
+
+
+def test_schedule_plan_host_logic(lib):
+    """The chunked-schedule planner (host arithmetic, no GPU).  Whole
+    resident waves (or a last wave at least 97 % full) keep the static
+    launch; otherwise about 24 items per resident block, chunks of at least
+    16 steps, every step covered exactly once by the chunks."""
+    # the headline: 1,024 blocks of 64 environments on 304 resident blocks (3.37 waves)
+    assert plan(lib, 1, 0, 1024, 1000, 304) == (8, 125)
+    # whole waves, a full last wave, one wave or less: static
+    assert plan(lib, 1, 0, 912, 1000, 304) == (0, 0)
+    assert plan(lib, 1, 0, 1213, 1000, 304) == (0, 0)   # 1213 / 1216 = 99.8 % full
+    assert plan(lib, 1, 0, 300, 1000, 304) == (0, 0)
+    # short rollouts: chunks of at least 16 steps; fewer than two chunks stay static
+    assert plan(lib, 1, 0, 1024, 100, 304) == (7, 16)
+    assert plan(lib, 1, 0, 1024, 31, 304) == (2, 16)
+    assert plan(lib, 1, 0, 1024, 16, 304) == (0, 0)
+    assert plan(lib, 1, 0, 1024, 1, 304) == (0, 0)
+    # the reverse pass: segments of K = 4 steps, at least 16 steps' worth per chunk
+    assert plan(lib, 1, 0, 2048, 250, 304, 4) == (4, 63)
+    # mode 0 never, mode 2 always with the given chunk
+    assert plan(lib, 0, 0, 1024, 1000, 304) == (0, 0)
+    assert plan(lib, 2, 3, 2, 10, 304) == (4, 3)
+    assert plan(lib, 2, 10, 2, 10, 304) == (0, 0)   # one chunk: nothing to schedule
+    # an item count that would not fit a launch grid stays static
+    assert plan(lib, 2, 1, 1 << 24, 1000, 304) == (0, 0)
+    for units, T, slots in [(1024, 1000, 304), (2048, 977, 456), (625, 40, 304), (5000, 333, 152)]:
+        n, s = plan(lib, 1, 0, units, T, slots)
+        if n:
+            assert s >= 16 and (n - 1) * s < T <= n * s
