@@ -546,12 +546,15 @@ Seg make_seg(const brax_system* s, int groups, int64_t n_envs) {
 }
 
 // Chunked schedule of a rollout of `units` blocks (Sched), per_sm of which
-// are resident per SM, over T steps (reverse pass: T checkpoint segments):
-// taken when the units leave the last resident wave less than 97 % full
-// (mode 1) or always (mode 2, chunks of `chunk` steps).  About 24 items per
-// resident block keep the final imbalance near one item; chunks of at least
-// min_chunk steps (16; in segments, 16 steps' worth) keep the cost of a chunk
-// boundary (the state through L2, a new block, one flag check) near 1 %.
+// are resident per SM, over T steps (reverse pass: T checkpoint segments).
+// Taken when the units leave the last resident wave less than 97 % full
+// (mode 1), or always (mode 2, chunks of `chunk` steps).  Mode 1 picks the
+// chunk length (at least min_chunk steps: 16, or 16 steps' worth of
+// segments) that minimises a round model of the launch: items run in rounds
+// of `slots` blocks in chunk-major order, a round lasts as long as its
+// longest item (a full chunk, or the shorter last chunk), and every item
+// costs a quarter step more (a new block, the state through L2, a flag
+// check).
 struct SchedPlan {
   int n_chunks = 0, chunk_steps = 0;
 };
@@ -565,8 +568,21 @@ SchedPlan plan_schedule_slots(int mode, int chunk, int64_t units, int T, int64_t
   } else {
     const int64_t waves = (units + slots - 1) / slots;
     if (units <= slots || (double)units >= 0.97 * (double)(waves * slots)) return p;
-    const int64_t want = (24 * slots + units - 1) / units;  // chunks per unit
-    steps = std::max<int64_t>(min_chunk, (T + want - 1) / want);
+    steps = 0;
+    double best = 0.0;
+    for (int64_t len = std::max(1, min_chunk); len <= (T + 1) / 2; ++len) {
+      const int64_t C = (T + len - 1) / len;
+      if (C < 2) continue;
+      const int64_t last = T - (C - 1) * len;
+      const int64_t rounds = (C * units + slots - 1) / slots;
+      const int64_t full = std::min(rounds, ((C - 1) * units + slots - 1) / slots);
+      const double t = (double)(full * len + (rounds - full) * last) + 0.25 * (double)(C * units) / (double)slots;
+      if (steps == 0 || t < best - 1e-9) {
+        best = t;
+        steps = len;
+      }
+    }
+    if (steps == 0) return p;
   }
   const int64_t C = (T + steps - 1) / steps;
   if (C < 2 || C * units > 0x3fffffff) return p;

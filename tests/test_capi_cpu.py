@@ -88,8 +88,8 @@ def plan(lib, mode, chunk, units, T, slots, min_chunk=16):
 def test_schedule_plan_host_logic(lib):
     """The chunked-schedule planner (host arithmetic, no GPU).  Whole
     resident waves (or a last wave at least 97 % full) keep the static
-    launch; otherwise about 24 items per resident block, chunks of at least
-    16 steps, every step covered exactly once by the chunks."""
+    launch; otherwise the chunk length (at least 16 steps) that fills the
+    last round of items best, every step covered exactly once."""
     # the headline: 1,024 blocks of 64 environments on 304 resident blocks (3.37 waves)
     assert plan(lib, 1, 0, 1024, 1000, 304) == (8, 125)
     # whole waves, a full last wave, one wave or less: static
@@ -97,7 +97,8 @@ def test_schedule_plan_host_logic(lib):
     assert plan(lib, 1, 0, 1213, 1000, 304) == (0, 0)   # 1213 / 1216 = 99.8 % full
     assert plan(lib, 1, 0, 300, 1000, 304) == (0, 0)
     # short rollouts: chunks of at least 16 steps; fewer than two chunks stay static
-    assert plan(lib, 1, 0, 1024, 100, 304) == (7, 16)
+    assert plan(lib, 1, 0, 1024, 100, 304) == (5, 20)  # 16.8 rounds of 20 steps, not 23.6 of 16
+    assert plan(lib, 1, 0, 2048, 1000, 304) == (4, 250)  # the reverse pass at K = 1: 26.9 rounds
     assert plan(lib, 1, 0, 1024, 31, 304) == (2, 16)
     assert plan(lib, 1, 0, 1024, 16, 304) == (0, 0)
     assert plan(lib, 1, 0, 1024, 1, 304) == (0, 0)
