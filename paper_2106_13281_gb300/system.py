@@ -167,15 +167,18 @@ class BraxSystem:
                                    _ptr(out.get("contact_count")), _stream()))
         return out
 
-    def rollout_streamed(self, h_state0, h_actions, h_state_T, chunk_steps: int = 100, bufs: dict | None = None):
+    def rollout_streamed(self, h_state0, h_actions, h_state_T, chunk_steps: int = 100, bufs: dict | None = None,
+                         first_steps: int = 16):
         """Rollout whose inputs live in pinned host memory: the actions stream
-        to the device in chunks of `chunk_steps` steps on a copy stream while
-        the previous chunk is being stepped (double-buffered), and the final
-        state is copied back into the pinned h_state_T.  A chunk is one
-        brax_rollout launch continuing from the previous chunk's state, so the
-        result equals one launch over all steps.  `bufs` (a dict, filled on
-        first use) keeps the device buffers between calls.  Returns the
-        number of kernel launches."""
+        to the device in chunks on a copy stream while the previous chunk is
+        being stepped (double-buffered), and the final state is copied back
+        into the pinned h_state_T.  Chunks start at `first_steps` steps and
+        double up to `chunk_steps`, so that the copy nothing overlaps (the
+        state and the first chunk) is short.  A chunk is one brax_rollout
+        launch continuing from the previous chunk's state, so the result
+        equals one launch over all steps.  `bufs` (a dict, filled on first
+        use) keeps the device buffers between calls.  Returns the number of
+        kernel launches."""
         N, T = h_state0.shape[0], h_actions.shape[0]
         if not (h_state0.is_pinned() and h_actions.is_pinned() and h_state_T.is_pinned()):
             raise ValueError("rollout_streamed: host tensors must be pinned")
@@ -195,7 +198,10 @@ class BraxSystem:
         with torch.cuda.stream(cs):
             cs.wait_stream(comp)  # the buffers' previous users are done
             st[0].copy_(h_state0, non_blocking=True)
-        chunks = [(t0, min(T, t0 + C)) for t0 in range(0, T, C)]
+        chunks, t0, n = [], 0, max(1, min(int(first_steps), C))
+        while t0 < T:
+            chunks.append((t0, min(T, t0 + n)))
+            t0, n = t0 + n, min(C, 2 * n)
 
         def upload(i):
             t0, t1 = chunks[i]

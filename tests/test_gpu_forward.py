@@ -351,8 +351,9 @@ def test_pair_launch_rejected_for_general_systems(brax):
 
 @pytest.mark.parametrize("name,drop", [("quadruped", 0.38), ("pendulum", 0.0)])
 def test_rollout_streamed_equals_one_launch(brax, name, drop):
-    """Actions streamed from pinned host memory in chunks (ragged last chunk)
-    give bitwise the state of one launch over all steps."""
+    """Actions streamed from pinned host memory in chunks (fixed, or
+    doubling from a short first chunk; ragged last chunk) give bitwise the
+    state of one launch over all steps."""
     d = S.SCENES[name]()
     sysm = brax(d)
     N, T = 100, 25
@@ -363,8 +364,12 @@ def test_rollout_streamed_equals_one_launch(brax, name, drop):
     ha = torch.from_numpy(a).pin_memory()
     out = torch.empty((N, sysm.B, 13)).pin_memory()
     bufs = {}
-    for chunk in (10, 7, 25, 100):
-        n = sysm.rollout_streamed(hs, ha, out, chunk_steps=chunk, bufs=bufs)
+    for chunk, first in ((10, 10), (7, 7), (25, 25), (100, 100), (10, 3), (8, 1), (100, 16)):
+        n = sysm.rollout_streamed(hs, ha, out, chunk_steps=chunk, bufs=bufs, first_steps=first)
         torch.cuda.synchronize()
-        assert n == math.ceil(T / min(chunk, T))
-        assert torch.equal(out, ref), chunk
+        sizes, t, k = [], 0, min(first, chunk, T)  # first_steps doubling up to chunk_steps
+        while t < T:
+            sizes.append(min(k, T - t))
+            t, k = t + k, min(chunk, 2 * k)
+        assert n == len(sizes), (chunk, first)
+        assert torch.equal(out, ref), (chunk, first)
