@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--checkpoint-every", type=int, default=0,
                    help="K of the fwd+bwd figure (0: picked by the autotuner)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    p.add_argument("--bwd-variant", type=int, default=-1,
+                   help="reverse-kernel launch-bounds variant 0..3 (default: the autotuner's or the smallest that fits)")
     p.add_argument("--e2e-first-steps", type=int, default=16,
                    help="first chunk of the streamed (e2e) rollout; later chunks double up to 250 steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -210,6 +212,10 @@ def run_ours(args):
     # launch configuration and checkpoint interval: picked by timing the
     # workload itself (brax_autotune), before any timed region
     tuning = {"autotuned": not args.no_autotune}
+    if args.bwd_variant >= 0:  # a fixed reverse-kernel launch (profiling runs without the autotuner)
+        from paper_2106_13281_gb300.binding import check as check_rc
+        check_rc(sysm._L.brax_system_set_backward_launch(sysm.handle, args.bwd_variant))
+        tuning["bwd_variant"] = args.bwd_variant
     K = args.checkpoint_every if args.checkpoint_every > 0 else 10
     if not args.no_autotune:
         r = sysm.autotune(state0, actions)
