@@ -26,6 +26,18 @@ def _f32(t, shape=None, name="tensor"):
     return t
 
 
+def stream_chunks(T: int, chunk_steps: int, first_steps: int = 16):
+    """Step ranges [t0, t1) of a streamed rollout: the first chunk has
+    first_steps steps, each next one twice the previous, up to chunk_steps;
+    together they cover 0..T once, in order."""
+    C = max(1, min(int(chunk_steps), T))
+    chunks, t0, n = [], 0, max(1, min(int(first_steps), C))
+    while t0 < T:
+        chunks.append((t0, min(T, t0 + n)))
+        t0, n = t0 + n, min(C, 2 * n)
+    return chunks
+
+
 class BraxSystem:
     """One system (Sec. 4.1 system specification) uploaded to the current GPU."""
 
@@ -198,10 +210,7 @@ class BraxSystem:
         with torch.cuda.stream(cs):
             cs.wait_stream(comp)  # the buffers' previous users are done
             st[0].copy_(h_state0, non_blocking=True)
-        chunks, t0, n = [], 0, max(1, min(int(first_steps), C))
-        while t0 < T:
-            chunks.append((t0, min(T, t0 + n)))
-            t0, n = t0 + n, min(C, 2 * n)
+        chunks = stream_chunks(T, C, first_steps)
 
         def upload(i):
             t0, t1 = chunks[i]

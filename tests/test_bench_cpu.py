@@ -25,3 +25,18 @@ def test_flop_table_covers_the_workloads():
         fl = bench.alg_flops(scene)
         cats = fl["by_category_per_env_step"]
         assert abs(sum(cats.values()) - fl["flops_per_env_step"]) < 1e-6 * fl["flops_per_env_step"]
+
+
+def test_stream_chunks_cover_the_rollout_once():
+    """Chunks of the streamed rollout (the e2e path): 16 steps first, then
+    doubling up to the chunk length, covering every step once, in order."""
+    from paper_2106_13281_gb300.system import stream_chunks
+    assert stream_chunks(1000, 250, 16) == [(0, 16), (16, 48), (48, 112), (112, 240), (240, 490), (490, 740),
+                                            (740, 990), (990, 1000)]
+    assert stream_chunks(25, 10, 10) == [(0, 10), (10, 20), (20, 25)]
+    assert stream_chunks(5, 100, 16) == [(0, 5)]
+    for T, C, F in [(1, 1, 1), (7, 3, 1), (100, 100, 16), (999, 37, 5), (64, 8, 100)]:
+        ch = stream_chunks(T, C, F)
+        assert ch[0][0] == 0 and ch[-1][1] == T
+        assert all(a[1] == b[0] for a, b in zip(ch, ch[1:]))
+        assert all(0 < t1 - t0 <= max(1, min(C, T)) for t0, t1 in ch)
