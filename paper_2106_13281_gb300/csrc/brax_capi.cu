@@ -486,6 +486,9 @@ std::mutex g_pool_mu;
 // Returns the offset of `blob` in the device's pool (uploading it to the
 // constant pools of the kernel translation units when it is new), -1 when
 // the pool is full, or -2 - cudaError when the upload failed.
+static_assert(alignof(SysP) <= 16 && alignof(BodyP) <= 16 && alignof(PairP) <= 16 && alignof(PlaneP) <= 16 &&
+                  alignof(SysP2) <= 16 && alignof(BodyP2) <= 16,
+              "blob sections and constant-pool ranges start on 16-byte boundaries");
 int pool_acquire(int device, const std::vector<unsigned char>& blob) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (auto& r : g_pool)
@@ -498,10 +501,12 @@ int pool_acquire(int device, const std::vector<unsigned char>& blob) {
   for (const auto& r : g_pool)
     if (r.device == device) used.push_back(&r);
   std::sort(used.begin(), used.end(), [](const PoolRange* a, const PoolRange* b) { return a->off < b->off; });
+  // first fit; ranges start on 16-byte boundaries (the parameter structs need
+  // 8, the blob sections are laid out from 16)
   int off = 0;
   for (const auto* r : used) {
     if (r->off - off >= bytes) break;
-    off = std::max(off, r->off + r->bytes);
+    off = std::max(off, (r->off + r->bytes + 15) & ~15);
   }
   if (off + bytes > kPoolBytes) return -1;
   cudaError_t e = upload_pool_forward(off, blob.data(), blob.size());
