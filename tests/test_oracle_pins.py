@@ -598,3 +598,151 @@ def test_reverse_op_count_is_additive():
     one, _ = orc.reverse_flops(free, st, np.zeros((1, 1, 0)))
     three, _ = orc.reverse_flops(free, st, np.zeros((3, 1, 0)))
     assert three == 3 * one
+
+
+# ----------------------------------------------------------------- two-body contacts, rotated anisotropic bodies
+def two_body_scene(kind, mu=1.0, e=0.0, seed=0):
+    """Two free bodies with distinct principal inertias, no gravity, no plane:
+    capsule-capsule or capsule-box.  One substep per step (h = 5 ms)."""
+    rng = np.random.default_rng(seed)
+    sb = S.SceneBuilder(dt=0.005, substeps=1, gravity=(0, 0, 0))
+    Ia = np.sort(rng.uniform(0.05, 0.6, size=3)) * [1.0, 1.7, 3.1]
+    a = sb.capsule_body("a", 1.7, 0.12, 0.7, (0, 0, 0), (0, 0, 1), friction=mu, inertia=Ia)
+    sb.colliders[-1]["elasticity"] = e
+    if kind == "capsule":
+        Ib = np.sort(rng.uniform(0.05, 0.6, size=3)) * [1.0, 2.3, 1.4]
+        b = sb.capsule_body("b", 0.9, 0.09, 0.5, (0, 0, 0), (0, 0, 1), friction=1.0, inertia=Ib)
+        cb = sb.collider_of(b)
+    else:
+        half = np.array([0.11, 0.07, 0.05])
+        b = sb.body("b", 0.8, S.box_inertia(0.8, half) * [1.0, 1.3, 0.7], (0, 0, 0))
+        cb = sb.collider(b, S.BOX, half=half, friction=1.0)
+    sb.colliders[cb]["elasticity"] = 1.0
+    sb.pair(sb.collider_of(a), cb)
+    return sb.build()
+
+
+def world_inv_inertia(q, inertia):
+    R = rotmats(q)
+    return R @ np.diag(1.0 / np.asarray(inertia)) @ R.T
+
+
+def momenta(desc, x, q, v, w):
+    """Linear and angular momentum (about the origin) computed here, from the
+    state and the descriptor alone: sum m v and sum x × m v + R diag(I) R^T w."""
+    P = np.zeros(3)
+    L = np.zeros(3)
+    for b in range(len(desc["mass"])):
+        m = desc["mass"][b]
+        R = rotmats(q[b])
+        P += m * v[b]
+        L += np.cross(x[b], m * v[b]) + R @ np.diag(desc["inertia"][b]) @ R.T @ w[b]
+    return P, L
+
+
+def touching_states(desc, rng, n_want):
+    """Random generic poses and velocities of the two bodies with exactly one
+    active contact after the kinematic integrator of the coming substep."""
+    h = desc["dt"] / desc["substeps"]
+    d1 = dict(desc, substeps=1, dt=h)
+    out = []
+    tries = 0
+    while len(out) < n_want and tries < 20000:
+        tries += 1
+        st = np.zeros((1, 2, 13))
+        for b in range(2):
+            st[0, b, 3:7] = axis_angle(rng.normal(size=3), rng.uniform(0.3, 3.0))
+            st[0, b, 7:10] = rng.normal(size=3) * 0.8
+            st[0, b, 10:13] = rng.normal(size=3) * 2.0
+        st[0, 0, 0:3] = rng.normal(size=3) * 0.05
+        st[0, 1, 0:3] = st[0, 0, 0:3] + rng.normal(size=3) * 0.17
+        post = orc.rollout(d1, st, np.zeros((1, 1, 0)))
+        pk = st.copy()
+        pk[0, :, 0:7] = post[0, :, 0:7]  # post-kinematic pose, pre-update velocities
+        cts = orc.contacts(desc, pk[0])
+        if len(cts) == 1 and cts[0][2] > 1e-4:
+            out.append((st, post, cts[0]))
+    assert len(out) == n_want, f"only {len(out)} touching configurations in {tries} tries"
+    return out
+
+
+@pytest.mark.parametrize("kind", ["capsule", "box"])
+@pytest.mark.parametrize("elasticity", [0.0, 0.5])
+def test_two_body_contact_conserves_momentum(kind, elasticity):
+    """Sec. 7.2 contact between two free bodies, rotated and with anisotropic
+    inertia (g = 0, no plane): the impulse is equal and opposite at one point,
+    so one substep conserves sum m v to roundoff and sum x × m v +
+    R diag(I) R^T w about the origin exactly (both taken at the post-kinematic
+    pose, before and after the collision integrator).  A sign error on the
+    second body, a swapped lever arm or a transposed world inertia breaks
+    one of the two."""
+    d = two_body_scene(kind, e=elasticity, seed=1)
+    rng = np.random.default_rng(10 + (kind == "box") + 2 * int(elasticity * 2))
+    n_moved = 0
+    for st, post, ct in touching_states(d, rng, 25):
+        x, q = post[0, :, 0:3], post[0, :, 3:7]
+        P0, L0 = momenta(d, x, q, st[0, :, 7:10], st[0, :, 10:13])
+        P1, L1 = momenta(d, x, q, post[0, :, 7:10], post[0, :, 10:13])
+        scale = 1.0 + np.abs(P0).max() + np.abs(L0).max()
+        assert np.abs(P1 - P0).max() < 1e-12 * scale
+        assert np.abs(L1 - L0).max() < 1e-10 * scale
+        n_moved += np.abs(post[0, :, 7:13] - st[0, :, 7:13]).max() > 1e-6
+    assert n_moved >= 12  # the contacts really changed the velocities
+    # several substeps in a row, each checked across its own collision update
+    st = touching_states(d, np.random.default_rng(99), 1)[0][0]
+    d1 = dict(d, substeps=1)
+    for _ in range(12):
+        post = orc.rollout(d1, st, np.zeros((1, 1, 0)))
+        x, q = post[0, :, 0:3], post[0, :, 3:7]
+        P0, L0 = momenta(d, x, q, st[0, :, 7:10], st[0, :, 10:13])
+        P1, L1 = momenta(d, x, q, post[0, :, 7:10], post[0, :, 10:13])
+        assert np.abs(P1 - P0).max() < 1e-12 * (1 + np.abs(P0).max())
+        assert np.abs(L1 - L0).max() < 1e-10 * (1 + np.abs(L0).max())
+        st = post
+
+
+@pytest.mark.parametrize("kind", ["capsule", "box"])
+def test_two_body_contact_velocity_changes(kind):
+    """One substep with one contact: body a changes by dv = J/m_a and
+    dw = R_a diag(1/I_a) R_a^T (l_a × J), body b by -J/m_b and
+    -R_b diag(1/I_b) R_b^T (l_b × J), with l = p - x at the contact point p
+    the oracle reports (Sec. 7.2; the world inverse inertia of Sec. 3 at the
+    post-kinematic orientation).  Without friction the normal relative
+    velocity afterwards is the Baumgarte/restitution target
+    max(beta depth / h, -e u_n) (velocity-level contact), which pins the
+    two-body effective mass."""
+    for mu, e in ((1.0, 0.0), (0.0, 0.0), (0.0, 0.5)):
+        d = two_body_scene(kind, mu=mu, e=e, seed=2)
+        h = d["dt"] / d["substeps"]
+        rng = np.random.default_rng(20 + (kind == "box"))
+        n_active = 0
+        for st, post, (ba, bb, depth, n, p) in touching_states(d, rng, 15):
+            assert (ba, bb) == (0, 1)
+            x, q = post[0, :, 0:3], post[0, :, 3:7]
+            dv = post[0, :, 7:10] - st[0, :, 7:10]
+            dw = post[0, :, 10:13] - st[0, :, 10:13]
+            J = d["mass"][0] * dv[0]
+            la, lb = p - x[0], p - x[1]
+            assert np.allclose(dv[1], -J / d["mass"][1], atol=1e-13, rtol=0)
+            assert np.allclose(dw[0], world_inv_inertia(q[0], d["inertia"][0]) @ np.cross(la, J), atol=1e-11, rtol=0)
+            assert np.allclose(dw[1], -world_inv_inertia(q[1], d["inertia"][1]) @ np.cross(lb, J), atol=1e-11, rtol=0)
+            u0 = (st[0, 0, 7:10] + np.cross(st[0, 0, 10:13], la)) - (st[0, 1, 7:10] + np.cross(st[0, 1, 10:13], lb))
+            un0 = float(u0 @ n)
+            jn = float(J @ n)
+            if mu == 0.0:
+                # no friction: the impulse is along n
+                assert np.linalg.norm(J - jn * n) < 1e-12 * (1 + abs(jn))
+                if jn > 0:
+                    u1 = (post[0, 0, 7:10] + np.cross(post[0, 0, 10:13], la)) - \
+                         (post[0, 1, 7:10] + np.cross(post[0, 1, 10:13], lb))
+                    target = max(d["baumgarte"] / h * depth, -e * un0)
+                    assert abs(float(u1 @ n) - target) < 1e-10 * (1 + abs(target))
+                    n_active += 1
+                else:  # separating faster than the target: no impulse
+                    assert max(d["baumgarte"] / h * depth, -e * un0) <= un0 + 1e-12
+            else:
+                # Coulomb: the normal part pushes a off b, the tangential part is capped by mu j_n
+                assert jn >= -1e-12
+                assert np.linalg.norm(J - jn * n) <= mu * jn + 1e-10
+        if mu == 0.0:
+            assert n_active >= 5
