@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--e2e-first-steps", type=int, default=16,
                    help="first chunk of the streamed (e2e) rollout; later chunks double up to 250 steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the other configurations (biped, adjoint, heterogeneous batch) in the headline run")
     p.add_argument("--workload", default="quadruped", choices=["quadruped", "biped", "adjoint", "hetero"],
                    help="quadruped: the headline line; the others time the remaining configurations "
                         "(biped forward 16384 x 1000; quadruped adjoint 4096 x 100 and x 1000; heterogeneous "
@@ -87,8 +89,9 @@ def kernel_sources_digest():
 
 
 def measured_traffic(key, path=None):
-    """DRAM bytes per launch of the dominant kernel from one ncu capture
-    (data/traffic.json), or None when the kernel sources changed since."""
+    """The small-case ncu capture of the dominant kernel recorded in
+    data/traffic.json under `key`, or None when the kernel sources changed
+    since (the counters then describe another kernel)."""
     p = path or os.path.join(ROOT, "paper_2106_13281_gb300", "data", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -96,7 +99,20 @@ def measured_traffic(key, path=None):
         rec = json.load(f).get(key)
     if not rec or rec.get("sources_sha256") != kernel_sources_digest():
         return None
-    return rec["dram_bytes_per_launch"]
+    return rec
+
+
+def scaled_traffic(rec, T, n_chunks, state_bytes):
+    """DRAM bytes of one full launch of T steps, scaled from a small capture
+    of the same kernel (rec: its steps, DRAM reads and the state bytes of its
+    environments).  The capture's reads beyond the initial state are the
+    per-step stream (the actions), which grows with the steps; the state is
+    read once and written once per chunk of the chunked schedule (a later
+    chunk's state was evicted from L2 by the actions streamed in between), so
+    reads = T x per-step + state x chunks and writes = state x chunks."""
+    per_step = (rec["dram_read_bytes"] - rec["state_bytes"]) / rec["steps"]
+    chunks = max(1, int(n_chunks))
+    return int(round(T * per_step + 2 * state_bytes * chunks))
 
 
 def alg_flops(scene="quadruped"):
@@ -248,6 +264,7 @@ def run_ours(args):
         end.record(stream)
         torch.cuda.synchronize()
     sysm.sync_status()
+    launch = sysm.last_rollout()
     total_ms = barrier_max(start.elapsed_time(end), world)
     kern_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
     envsteps = N * T
@@ -317,6 +334,14 @@ def run_ours(args):
 
     # state read and written once, actions read once (the per-launch algorithmic bytes)
     algorithmic_bytes = 2 * state0.numel() * 4 + actions.numel() * 4
+    # DRAM traffic of the timed launch, scaled from the small-case capture of the same kernel
+    rec = measured_traffic(f"quadruped_pair_{N}") if world == 1 else None
+    traffic, traffic_note = None, "no capture of the current kernel sources"
+    if rec is not None and tuning.get("fwd_kernel", "two_envs_per_thread") == "two_envs_per_thread":
+        traffic = scaled_traffic(rec, T, launch["n_chunks"], state0.numel() * 4)
+        traffic_note = (f"scaled from one ncu capture of {rec['kernel']} at {N} envs x {rec['steps']} steps "
+                        f"(dram read {rec['dram_read_bytes']} B, write {rec['dram_write_bytes']} B) to "
+                        f"{T} steps in {max(1, launch['n_chunks'])} chunk(s)")
     fl = alg_flops("quadruped")
     flops_per_envstep = fl["flops_per_env_step"]
     achieved_tflops = flops_per_envstep * envsteps / (kern_ms / 1e3) / 1e12
@@ -350,15 +375,20 @@ def run_ours(args):
                     "loss": "-(torso x displacement); gradients w.r.t. the action sequence and the initial state"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                     "traffic": measured_traffic(f"quadruped_{N}x{T}") if world == 1 else None,
+                     "traffic": traffic, "traffic_note": traffic_note,
                      "algorithmic_bytes": algorithmic_bytes,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                      "flops_per_env_step": flops_per_envstep, "kernel_ms": kern_ms},
         "clocks": clk.summary(),
-        "tuning": tuning,
+        "tuning": dict(tuning, launch=launch),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(d, sysm, seed)
+    if rank == 0 and world == 1 and not args.no_secondary:
+        # the other configurations of the method, timed in the same run
+        with Clocks(local) as clk2:
+            other = {w: workload_lines(args, w) for w in ("biped", "adjoint", "hetero")}
+        line["configs_other"] = dict(other, clocks=clk2.summary())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -441,8 +471,16 @@ def _timed(fn, warmup, steps):
 
 
 def run_workload(args):
-    """The other configurations of the method, one JSON line each (not the
-    headline): biped forward, quadruped adjoint, heterogeneous batch."""
+    """One other configuration of the method (--workload), one JSON line per
+    figure (not the headline)."""
+    for ln in workload_lines(args, args.workload):
+        print(json.dumps(ln), flush=True)
+
+
+def workload_lines(args, workload):
+    """The other configurations of the method: biped forward, quadruped
+    adjoint (100 and 1,000 steps), heterogeneous batch fwd+bwd; a list of
+    result dicts."""
     import numpy as np
     import torch
 
@@ -464,7 +502,7 @@ def run_workload(args):
                 "frac": t / FP32_PEAK_TFLOPS, "flops_per_env_step": flops_per_envstep}
 
     lines = []
-    if args.workload == "biped":
+    if workload == "biped":
         N, T = 16384, 1000
         d, sysm, st, a = setup("biped", N, T, 2)
         r = sysm.autotune(st, a)
@@ -476,7 +514,7 @@ def run_workload(args):
                       "config": {"workload": "biped-17body forward rollout, 16384 envs x 1000 steps x 10 substeps"},
                       "roofline": roof(alg_flops("biped")["flops_per_env_step"], N * T, ms),
                       "tuning": {k: r[k] for k in ("fwd_kernel", "fwd_groups", "fwd_variant")}})
-    elif args.workload == "adjoint":
+    elif workload == "adjoint":
         for T in (100, 1000):
             N = 4096
             d, sysm, st, a = setup("quadruped", N, T, 3, drop=0.0)
@@ -551,7 +589,7 @@ def run_workload(args):
                       "tuning": {"warps_per_block": warps}, "cuda_graph": True})
     for ln in lines:
         ln.update({"n_gpus": 1, "warmup": args.warmup, "dtype": "f32", "data": "synthetic", "higher_is_better": True})
-        print(json.dumps(ln), flush=True)
+    return lines
 
 
 def main():

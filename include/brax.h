@@ -22,9 +22,15 @@
  *  - Arrays passed to compute calls are device pointers unless stated,
  *    contiguous, caller-owned; calls are asynchronous on `stream` (a
  *    cudaStream_t passed as void*, NULL = the legacy default stream).
- *  - Compute calls allocate nothing; scratch memory comes from the caller
- *    (brax_workspace_size).  Device memory for a system's parameters and its
- *    status word is allocated once by brax_system_create.
+ *  - Device memory for a system's parameters and its status word is
+ *    allocated once by brax_system_create; the reverse pass's workspace comes
+ *    from the caller (brax_workspace_size).  The one allocation a compute
+ *    call can make is the chunked schedule's scratch (a ring of four regions
+ *    of (32 + blocks) int32, a few KB): brax_rollout, brax_rollout_backward
+ *    and the batch rollouts allocate it the first time a launch takes the
+ *    chunked schedule (see brax_rollout) or needs a larger one; a call made
+ *    while its stream is being captured takes the static schedule instead of
+ *    allocating.  brax_step and brax_rollout_backward_noalloc never allocate.
  *  - Angles in the descriptor are degrees (App. A angle_limit); angles passed
  *    to brax_default_qp are radians.
  *  - Error messages: brax_last_error() (thread-local).
@@ -170,15 +176,62 @@ int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, con
  * must not overlap the actions, checkpoints or torso arrays) once a
  * per-block flag says that chunk is done.  Results are bitwise those of the
  * static schedule.  The flags and the counter live in scratch the system
- * owns (four regions used in turn by successive calls, so up to four
- * rollouts of one system may overlap on the GPU); the first call that needs
- * more of it allocates, and a call made while its stream is being captured
- * that would need to allocate takes the static schedule.  A wait gives up
- * after 2 s: the rollout stops, its outputs are incomplete and
- * brax_sync_status reports BRAX_ERR_TIMEOUT. */
+ * owns: four regions used in turn by successive chunked launches of the
+ * system (forward and reverse), each zeroed on the launch's stream when it is
+ * taken.  So at most four chunked launches of one system may be in flight on
+ * the GPU at once: a fifth (on another stream), or an eager launch between
+ * replays of a captured CUDA graph that holds one of the regions, can zero a
+ * region a running kernel still uses and silently corrupt its results.  The
+ * first call that needs more scratch allocates, and a call made while its
+ * stream is being captured that would need to allocate takes the static
+ * schedule.  A wait gives up after 2 s: the rollout stops, its outputs are
+ * incomplete and brax_sync_status reports BRAX_ERR_TIMEOUT. */
 int brax_rollout(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj,
                  int32_t* contact_count, void* stream);
+
+/* ------------------------------------------------------------ environment layer
+ * The gym-like environment of Sec. 4.2: the book-keeping of a sequential
+ * decision problem (observing, rewarding, ending and resetting episodes)
+ * computed by the rollout kernel itself after every step, so a policy
+ * training loop needs no extra launch per step.  The paper prints no
+ * observation or reward formula; this layer reads them as follows.
+ *   Observation after each step, obs_dim = 11 + 2 * (total joint DOF):
+ *     [0]      the root body's (body 0) height z,
+ *     [1..4]   its quaternion (w, x, y, z),
+ *     [5..7]   its velocity, [8..10] its angular velocity,
+ *     then every joint DOF's angle (joint order, axes 0..dof-1; radians,
+ *     measured as the limits measure them), then every joint DOF's angular
+ *     rate: (w_child - w_parent) along the DOF's world axis.
+ *   Reward of the step t -> t+1 (a MuJoCo-like locomotion reward; App. E:
+ *   the Brax Ant drops the contact cost, as here):
+ *     forward_weight * (x_root(t+1) - x_root(t)) / dt
+ *     + healthy_reward * (not done) - ctrl_cost * sum_a clamp(a, -1, 1)^2.
+ *   done: the root's height after the step lies outside [min_z, max_z].
+ *   Auto reset: a done environment continues from its row of reset_state at
+ *   the next step; its observation of the done step is the terminal one
+ *   (before the reset).  */
+typedef struct {
+  float forward_weight;  /* reward per metre per second of root progress along x */
+  float healthy_reward;  /* reward per step while not done */
+  float ctrl_cost;       /* cost per unit of squared clamped action */
+  float min_z, max_z;    /* healthy range of the root's height (m) */
+  int32_t auto_reset;    /* 1: done environments restart from reset_state */
+} brax_env_params;
+
+/* Observation size of a system's environment layer: 11 + 2 * total joint DOF. */
+int brax_env_obs_size(const brax_system* sys, int32_t* obs_dim);
+
+/* T steps of the environment in one persistent launch (the physics of
+ * brax_rollout, with its kernel choice and schedule).  Device arrays:
+ *   state0 [N,B,13], actions [T,N,A], reset_state [N,B,13] (required with
+ *   auto_reset, else may be NULL), state_T [N,B,13] (the state after the
+ *   last step and its reset), obs [T,N,obs_dim], reward [T,N], done [T,N]
+ *   (uint8, 0/1).  Errors: INVALID_ARGUMENT (null arrays, min_z > max_z),
+ *   CUDA.  Allocation and concurrency as brax_rollout. */
+int brax_env_rollout(const brax_system* sys, const brax_env_params* env, int64_t n_envs, int32_t T,
+                     const float* state0, const float* reset_state, const float* actions, float* state_T, float* obs,
+                     float* reward, uint8_t* done, void* stream);
 
 /* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K). */
 int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, size_t* bytes);
@@ -189,7 +242,10 @@ int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32
  * and g_torso_traj [T,N,3] (NULL = zero).  Outputs g_actions [T,N,A] and
  * g_state0 [N,B,13] (either may be NULL).  The forward is recomputed from
  * each checkpoint segment on chip.  workspace: device scratch of at least
- * brax_workspace_size bytes, 256-byte aligned. */
+ * brax_workspace_size bytes, 256-byte aligned.  When the blocks do not fill
+ * a whole number of resident waves the launch takes the chunked schedule of
+ * brax_rollout over checkpoint segments (last first), with the same scratch
+ * ring, allocation and concurrency limit. */
 int brax_rollout_backward(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                           const float* actions, const float* checkpoints, const float* g_state_T,
                           const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
@@ -206,9 +262,13 @@ int brax_rollout_backward(const brax_system* sys, int64_t n_envs, int32_t T, int
  * more scratch than the array holds (brax_workspace_size says how much);
  * BRAX_ERR_CUDA if the array's address cannot be looked up.  The first call
  * on a device looks up the array's device address (once per device); make it
- * before any stream capture.  Calls share the array, which keeps the last
- * call's contents (nothing in it needs to start at zero); calls whose
- * kernels overlap on the GPU race on it.  Allocates nothing. */
+ * before any stream capture.  The array holds the workspace and, behind it,
+ * the chunked schedule's counter and flags (zeroed on the stream by every
+ * call that takes that schedule); when they do not fit beside the workspace
+ * the launch takes the static schedule.  Calls share the array, which keeps
+ * the last call's contents (nothing else in it needs to start at zero);
+ * calls whose kernels overlap on the GPU race on it.  Allocates nothing, in
+ * every schedule mode. */
 #define BRAX_NOALLOC_SCRATCH_BYTES (32u << 20)
 int brax_rollout_backward_noalloc(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                                   const float* actions, const float* checkpoints, const float* g_state_T,
@@ -228,8 +288,10 @@ int brax_batch_offsets(const brax_batch* batch, int32_t T, int32_t K, int32_t i,
 /* One launch over every system of the batch (brax_rollout's arguments, as
  * concatenated blocks).  It takes the chunked schedule described at
  * brax_rollout when the batch's blocks do not fill a whole number of resident
- * waves (the scratch is the batch's; a wait that gives up is reported by the
- * brax_sync_status of the system whose environments were waited for). */
+ * waves (the scratch is the batch's, with the same allocation on first need
+ * and the same limit of four chunked launches of the batch in flight; a wait
+ * that gives up is reported by the brax_sync_status of the system whose
+ * environments were waited for). */
 int brax_batch_rollout(const brax_batch* batch, int32_t T, int32_t K, const float* state0, const float* actions,
                        float* state_T, float* checkpoints, float* torso_traj, void* stream);
 int brax_batch_workspace_size(const brax_batch* batch, int32_t T, int32_t K, size_t* bytes);

@@ -125,6 +125,7 @@ def lib():
             L.orc_jvp.argtypes = [P, i64, i32, P, P, P, P, P, P, i32]
             L.orc_default_qp.argtypes = [P, i64, P, P, P, P]
             L.orc_joint_angles.argtypes = [P, i64, P, P]
+            L.orc_joint_state.argtypes = [P, i64, P, P, P]
             L.orc_energy.argtypes = [P, i64, P, P, P]
             L.orc_contacts.argtypes = [P, P, i32, P, P]
             L.orc_segment_closest.argtypes = [P, P, P, P, P]
@@ -238,6 +239,17 @@ def joint_angles(system, state):
     out = np.zeros((state.shape[0], s.D))
     lib().orc_joint_angles(C.byref(s.c), state.shape[0], _p(state), _p(out))
     return out
+
+
+def joint_state(system, state):
+    """Joint angles [N, D] and joint angular rates [N, D] (w_c - w_p along each
+    joint axis in the world)."""
+    s = _sys(system)
+    state = _f64(state)
+    ang = np.zeros((state.shape[0], s.D))
+    rate = np.zeros((state.shape[0], s.D))
+    lib().orc_joint_state(C.byref(s.c), state.shape[0], _p(state), _p(ang), _p(rate))
+    return ang, rate
 
 
 def energy_momentum(system, state):

@@ -338,6 +338,31 @@ int orc_joint_angles(const orc_desc* d, int64_t N, const double* state, double* 
   return 0;
 }
 
+// Joint angles [N, D] and joint angular rates [N, D]: for each joint DOF the
+// relative angular velocity of child and parent, w_c - w_p, along the joint
+// axis in the world, R_p (parent joint-frame axis k).  The observation of the
+// gym-like environment layer (Sec. 4.2) reads both.
+int orc_joint_state(const orc_desc* d, int64_t N, const double* state, double* ang_out, double* rate_out) {
+  System s = make_system(d);
+  for (int64_t n = 0; n < N; ++n) {
+    std::vector<Body<double>> qp;
+    load_env(s, state + n * s.B * 13, qp);
+    std::vector<Frame<double>> fr(s.B);
+    for (int b = 0; b < s.B; ++b) fr[b] = frame(s, b, qp[b]);
+    for (int j = 0; j < s.J; ++j) {
+      double ang[3];
+      V3<double> P[3];
+      joint_angles(s, j, fr[s.parent[j]], fr[s.child[j]], ang, P);
+      const V3<double> wr = qp[s.child[j]].w - qp[s.parent[j]].w;
+      for (int a = 0; a < s.dof[j]; ++a) {
+        ang_out[n * s.D + s.dof_offset[j] + a] = ang[a];
+        rate_out[n * s.D + s.dof_offset[j] + a] = dot(wr, P[a]);
+      }
+    }
+  }
+  return 0;
+}
+
 // Energy [N] and momentum [N, 6] (linear, angular about the origin).
 int orc_energy(const orc_desc* d, int64_t N, const double* state, double* energy_out, double* momentum_out) {
   System s = make_system(d);

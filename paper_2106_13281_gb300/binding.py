@@ -24,7 +24,7 @@ EXPORTS = ["brax_system_create", "brax_system_destroy", "brax_system_info", "bra
            "brax_rollout", "brax_workspace_size", "brax_rollout_backward", "brax_batch_create",
            "brax_batch_destroy", "brax_batch_offsets", "brax_batch_rollout", "brax_batch_workspace_size",
            "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error", "brax_rollout_backward_noalloc",
-           "brax_autotune", "brax_batch_autotune"]
+           "brax_autotune", "brax_batch_autotune", "brax_env_obs_size", "brax_env_rollout"]
 
 BRAX_TUNE_FORWARD, BRAX_TUNE_REVERSE = 1, 2
 
@@ -33,6 +33,11 @@ class BraxError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"brax error {code} ({STATUS.get(code, '?')}): {msg}")
         self.code = code
+
+
+class brax_env_params(C.Structure):
+    _fields_ = [("forward_weight", C.c_float), ("healthy_reward", C.c_float), ("ctrl_cost", C.c_float),
+                ("min_z", C.c_float), ("max_z", C.c_float), ("auto_reset", C.c_int32)]
 
 
 class brax_tune_result(C.Structure):
@@ -105,6 +110,8 @@ def load_library(path: str = LIB_PATH):
         L.brax_autotune.argtypes = [P, i64, i32, P, P, i32, C.c_size_t, P, C.POINTER(brax_tune_result)]
         L.brax_batch_autotune.argtypes = [P, i32, i32, P, P, i32, P, C.POINTER(i32), C.POINTER(C.c_float)]
         L.brax_rollout_backward_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P]
+        L.brax_env_obs_size.argtypes = [P, C.POINTER(i32)]
+        L.brax_env_rollout.argtypes = [P, C.POINTER(brax_env_params), i64, i32, P, P, P, P, P, P, P, P]
         if hasattr(L, "brax_system_set_launch"):
             L.brax_system_set_launch.argtypes = [P, i32, i32]
         if hasattr(L, "brax_system_set_pair_launch"):
@@ -112,6 +119,10 @@ def load_library(path: str = LIB_PATH):
             L.brax_system_get_launch.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
             L.brax_system_get_pair_launch.argtypes = [P, C.POINTER(i32)]
             L.brax_system_set_backward_launch.argtypes = [P, i32]
+        if hasattr(L, "brax_system_last_rollout"):
+            L.brax_system_last_rollout.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
+        if hasattr(L, "brax_internal_atan2"):
+            L.brax_internal_atan2.argtypes = [P, P, P, P, i64, P]
         if hasattr(L, "brax_system_set_schedule"):
             L.brax_system_set_schedule.argtypes = [P, i32, i32, i32, i64]
             L.brax_batch_set_schedule.argtypes = [P, i32, i32]

@@ -68,6 +68,19 @@ __device__ __forceinline__ void load_body_ws(const float* p, int stride, Body& s
   s.v = mk3(p[7 * stride], p[8 * stride], p[9 * stride]);
   s.w = mk3(p[10 * stride], p[11 * stride], p[12 * stride]);
 }
+// Drop one 128-byte line of the workspace from L2 without writing it back:
+// the reverse sweep has read it for the last time before the next recompute
+// overwrites it, so writing it back to DRAM would move dead data.
+__device__ __forceinline__ void discard_line(const float* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+// Lane i < 13 drops field i's line of a lane-contiguous state (13 rows of
+// 32 floats, `stride` floats apart).  Called once the warp has consumed the
+// state (after a __syncwarp).
+__device__ __forceinline__ void discard_state_ws(const float* row0, int stride, int lane) {
+  if (lane < 13) discard_line(row0 + (int64_t)lane * stride);
+}
+
 __device__ __forceinline__ void store_body_ws(float* p, int stride, const Body& s) {
   p[0] = s.x.x;
   p[stride] = s.x.y;
@@ -297,8 +310,8 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
 // schedule (Sched; chunk_steps counts segments, chunk 0 holds the last
 // ones), one chunk of the unit of the item it takes; the state adjoint then
 // passes from chunk to chunk through the workspace.
-template <int MAXT, int MINB, bool kGeneral>
-__global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_constant__ Launch L) {
+template <bool kGeneral>
+__device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   const bool chunked = L.sc.n_chunks > 0;
@@ -429,6 +442,8 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
     for (int t = t1 - 1; t >= t0; --t) {
       load_body_ws(ws_steps + (int64_t)(t - t0) * 13 * stride, stride, s);
       load_act(t);
+      __syncwarp();
+      discard_state_ws(ws_steps - lane + (int64_t)(t - t0) * 13 * stride, stride, lane);
       for (int k = 0; k < nsub; ++k) {
         store_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, s);
         if (k + 1 < nsub)
@@ -444,6 +459,8 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
         load_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, sin);
         bwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bm, bar, nthr, sin, gs, act,
                               gact);
+        __syncwarp();
+        discard_state_ws(ws_subs - lane + (int64_t)k * 13 * stride, stride, lane);
       }
       if (valid && sg.g_actions && (bp.flags & kHasParent)) {
         float* ga = sg.g_actions + ((int64_t)t * N + env) * A;
@@ -482,6 +499,26 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_co
   }
 }
 
+// Launch-bounds variants 0..3 (as the forward kernels), and variant 4: at
+// most 112 registers a thread (blocks of up to 576 threads; two 9-warp
+// groups per SM), which holds more of the adjoint's live values than the
+// 96 registers (576, 1) gives.
+template <int MAXT, int MINB, bool kGeneral>
+__global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_constant__ Launch L) {
+  rollout_bwd_body<kGeneral>(L);
+}
+template <bool kGeneral>
+__global__ void __maxnreg__(112) rollout_bwd_kernel_r112(const __grid_constant__ Launch L) {
+  rollout_bwd_body<kGeneral>(L);
+}
+
+template <class KernelT>
+static int bwd_occupancy_k(KernelT k, int threads, size_t smem) {
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
+}
 template <int MAXT, int MINB, bool G>
 static int bwd_occupancy_t(int threads, size_t smem) {
   auto k = rollout_bwd_kernel<MAXT, MINB, G>;
@@ -491,6 +528,9 @@ static int bwd_occupancy_t(int threads, size_t smem) {
   return n;
 }
 int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem) {
+  if (variant == 4)
+    return general ? bwd_occupancy_k(rollout_bwd_kernel_r112<true>, threads, smem)
+                   : bwd_occupancy_k(rollout_bwd_kernel_r112<false>, threads, smem);
   if (general) {
     switch (variant) {
       case 0: return bwd_occupancy_t<384, 2, true>(threads, smem);
@@ -516,8 +556,24 @@ static cudaError_t launch_bwd_t(const Launch& L, int grid, int threads, size_t s
   return cudaGetLastError();
 }
 
+template <class KernelT>
+static cudaError_t launch_bwd_k(KernelT k, const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+int backward_variant_max_threads(int variant) {
+  static const int t[5] = {384, 576, 1024, 288, 576};
+  return (variant >= 0 && variant < 5) ? t[variant] : 0;
+}
+
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st) {
+  if (variant == 4)
+    return general ? launch_bwd_k(rollout_bwd_kernel_r112<true>, L, grid, threads, smem, st)
+                   : launch_bwd_k(rollout_bwd_kernel_r112<false>, L, grid, threads, smem, st);
   if (general) {
     switch (variant) {
       case 0: return launch_bwd_t<384, 2, true>(L, grid, threads, smem, st);
@@ -611,6 +667,13 @@ extern "C" int brax_rollout_backward_noalloc(const brax_system* s, int64_t n_env
   if (e != cudaSuccess)
     return noalloc_fail(BRAX_ERR_CUDA, std::string("brax_rollout_backward_noalloc: cudaGetSymbolAddress: ") +
                                            cudaGetErrorString(e));
-  return brax_rollout_backward(s, n_envs, T, K, state0, actions, checkpoints, g_state_T, g_torso_traj, g_actions,
-                               g_state0, ws, (size_t)BRAX_NOALLOC_SCRATCH_BYTES, stream);
+  // The array holds the reverse pass's workspace first and, behind it (at a
+  // 256-byte boundary), the region a chunked schedule takes its ticket
+  // counter and flags from; when that region does not fit the launch takes
+  // the static schedule.  Either way nothing is allocated.
+  const size_t ws_bytes = (need + 255) & ~(size_t)255;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  return rollout_backward_fixed_sched(s, n_envs, T, K, state0, actions, checkpoints, g_state_T, g_torso_traj, g_actions,
+                                      g_state0, ws, ws_bytes, reinterpret_cast<int32_t*>(base + ws_bytes),
+                                      (size_t)BRAX_NOALLOC_SCRATCH_BYTES - ws_bytes, stream);
 }

@@ -388,6 +388,8 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   S.D = D;
   S.P = Pb;
   S.n_planes = (int)planes.size();
+  S.flat = 1;
+  for (const PlaneP& pl : planes) S.flat = S.flat && pl.n[0] == 0.f && pl.n[1] == 0.f && pl.n[2] == 1.f;
   S.substeps = d.substeps;
   S.average = d.average_contacts ? 1 : 0;
   S.general = Pb > 0 ? 1 : 0;
@@ -637,14 +639,29 @@ void sched_free(SchedScratch& sc) {
   sc.retired.clear();
 }
 
+// A caller-provided scheduler region: `fixed` (device memory of `bytes`
+// bytes) is used instead of the system's own scratch; with use = true and a
+// region too small (or null) the launch takes the static schedule, so that
+// nothing is allocated.
+struct FixedRegion {
+  bool use = false;
+  int32_t* fixed = nullptr;
+  size_t bytes = 0;
+};
+
 // Fill L.sc for a chunked launch of `units` units when the plan asks for one
 // and scratch can be had; returns the grid (one block per item, or `units`).
 // Fails only if zeroing the scratch region fails.
 cudaError_t apply_schedule(const SchedPlan& pl, SchedScratch& sc, int first_item, int64_t wait_ns, int64_t units,
-                           Launch& L, int64_t* grid, cudaStream_t st) {
+                           Launch& L, int64_t* grid, cudaStream_t st, const FixedRegion& fr = FixedRegion{}) {
   *grid = units;
   if (pl.n_chunks == 0) return cudaSuccess;
-  int32_t* region = sched_region(sc, units, st);
+  int32_t* region = nullptr;
+  if (fr.use) {
+    if (fr.fixed && fr.bytes >= (size_t)(32 + units) * sizeof(int32_t)) region = fr.fixed;
+  } else {
+    region = sched_region(sc, units, st);
+  }
   if (!region) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(region, 0, (32 + units) * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
@@ -750,7 +767,7 @@ int brax_system_set_launch(brax_system* s, int32_t groups, int32_t variant) {
 // Two-environments-per-thread launch override (mode 0: off, 1: on; groups of
 // 64 environments per block; launch-bounds variant); used by the autotuner.
 int brax_system_set_pair_launch(brax_system* s, int32_t mode, int32_t groups, int32_t variant) {
-  if (!s || mode < 0 || mode > 1 || groups < 1 || groups > 15 || variant < 0 || variant > 3)
+  if (!s || mode < 0 || mode > 1 || groups < 1 || groups > 15 || variant < 0 || variant > 4)
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_pair_launch: bad arguments");
   if (mode == 1 && !s->paired)
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_pair_launch: the system has no paired kernel");
@@ -796,8 +813,8 @@ int brax_system_get_pair_launch(const brax_system* s, int32_t* mode) {
   return BRAX_OK;
 }
 int brax_system_set_backward_launch(brax_system* s, int32_t variant) {
-  if (!s || variant < -1 || variant > 3) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_backward_launch: bad arguments");
-  if (variant >= 0 && 32 * s->B > rollout_variant_max_threads(variant))
+  if (!s || variant < -1 || variant > 4) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_backward_launch: bad arguments");
+  if (variant >= 0 && 32 * s->B > backward_variant_max_threads(variant))
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_set_backward_launch: block too large for the variant");
   s->bwd_variant = variant;
   return BRAX_OK;
@@ -810,9 +827,36 @@ int brax_default_qp(const brax_system* s, int64_t n_envs, const float* root_pos,
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_default_qp");
 }
 
-int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+}  // extern "C"
+
+namespace {
+// Outputs and parameters of the environment layer for one rollout (null: off).
+struct EnvOut {
+  const brax_env_params* p;
+  const float* reset_state;
+  float* obs;
+  float* reward;
+  uint8_t* done;
+};
+void apply_env(const brax_system* s, Seg& sg, const EnvOut* env) {
+  if (!env) return;
+  const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
+  sg.obs = env->obs;
+  sg.reward = env->reward;
+  sg.done = env->done;
+  sg.reset_state = env->reset_state;
+  sg.obs_dim = 11 + 2 * S->D;
+  sg.auto_reset = env->p->auto_reset ? 1 : 0;
+  sg.fwd_w_dt = (float)((double)env->p->forward_weight / ((double)S->h * S->substeps));
+  sg.healthy = env->p->healthy_reward;
+  sg.ctrl_cost = env->p->ctrl_cost;
+  sg.min_z = env->p->min_z;
+  sg.max_z = env->p->max_z;
+}
+
+int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj, int32_t* contact_count,
-                 void* stream) {
+                 void* stream, const EnvOut* env) {
   if (!s || n_envs < 0 || T < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: bad arguments");
   if (n_envs > 0 && (!state0 || !state_T || (T > 0 && s->A > 0 && !actions)))
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: null state or actions");
@@ -841,6 +885,7 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     sg.ckpt = checkpoints;
     sg.torso = torso_traj;
     sg.ccount = contact_count;
+    apply_env(s, sg, env);
     L.seg[0] = sg;
     const size_t smem = s->pair_groups * pair_group_bytes(s->B);
     const int threads = 32 * s->B * s->pair_groups;
@@ -849,8 +894,12 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     int64_t launch_grid;
     cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
                                    as_stream(stream));
+    s->last_grid = launch_grid;
+    s->last_chunks = L.sc.n_chunks;
+    s->last_chunk_steps = L.sc.chunk_steps;
     if (e == cudaSuccess)
-      e = launch_rollout_pair(L, (int)launch_grid, threads, smem, s->pair_variant, as_stream(stream));
+      e = launch_rollout_pair(L, (int)launch_grid, threads, smem, s->pair_variant,
+                              reinterpret_cast<const SysP*>(s->blob.data())->flat != 0, as_stream(stream));
     return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
   }
   Seg sg = make_seg(s, s->groups, n_envs);
@@ -865,6 +914,7 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   sg.ckpt = checkpoints;
   sg.torso = torso_traj;
   sg.ccount = contact_count;
+  apply_env(s, sg, env);
   L.seg[0] = sg;
   const size_t smem = s->groups * group_bytes(s);
   const int threads = 32 * s->B * s->groups;
@@ -873,8 +923,41 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   int64_t launch_grid;
   cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
                                  as_stream(stream));
+  s->last_grid = launch_grid;
+  s->last_chunks = L.sc.n_chunks;
+  s->last_chunk_steps = L.sc.chunk_steps;
   if (e == cudaSuccess) e = launch_rollout(L, (int)launch_grid, threads, smem, s->variant, s->general, as_stream(stream));
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout");
+}
+
+}  // namespace
+
+extern "C" {
+
+int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                 const float* actions, float* state_T, float* checkpoints, float* torso_traj, int32_t* contact_count,
+                 void* stream) {
+  return rollout_impl(s, n_envs, T, K, state0, actions, state_T, checkpoints, torso_traj, contact_count, stream,
+                      nullptr);
+}
+
+int brax_env_obs_size(const brax_system* s, int32_t* obs_dim) {
+  if (!s || !obs_dim) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_env_obs_size: null argument");
+  *obs_dim = 11 + 2 * s->D;
+  return BRAX_OK;
+}
+
+int brax_env_rollout(const brax_system* s, const brax_env_params* env, int64_t n_envs, int32_t T, const float* state0,
+                     const float* reset_state, const float* actions, float* state_T, float* obs, float* reward,
+                     uint8_t* done, void* stream) {
+  if (!s || !env || n_envs < 0 || T < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_env_rollout: bad arguments");
+  if (n_envs > 0 && T > 0 && (!obs || !reward || !done || (env->auto_reset && !reset_state)))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_env_rollout: obs, reward and done are required (and reset_state "
+                                           "with auto_reset)");
+  if (!(env->min_z <= env->max_z))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_env_rollout: min_z must not exceed max_z");
+  EnvOut eo{env, reset_state, obs, reward, done};
+  return rollout_impl(s, n_envs, T, 1, state0, actions, state_T, nullptr, nullptr, nullptr, stream, &eo);
 }
 
 int brax_step(const brax_system* s, int64_t n_envs, const float* state_in, const float* actions, float* state_out,
@@ -1054,10 +1137,11 @@ extern "C" int brax_workspace_size(const brax_system* s, int64_t n_envs, int32_t
   return BRAX_OK;
 }
 
-extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
-                                     const float* actions, const float* checkpoints, const float* g_state_T,
-                                     const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
-                                     size_t workspace_bytes, void* stream) {
+namespace {
+int rollout_backward_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                          const float* actions, const float* checkpoints, const float* g_state_T,
+                          const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                          size_t workspace_bytes, void* stream, const FixedRegion& fr) {
   if (!s || n_envs < 0 || T < 0 || K < 1) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: bad arguments");
   if (n_envs == 0) return BRAX_OK;
   if (!g_state_T) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: g_state_T is required");
@@ -1099,17 +1183,40 @@ extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32
   L.seg[0] = sg;
   const int threads = 32 * s->B;
   const int variant =
-      (s->bwd_variant >= 0 && threads <= rollout_variant_max_threads(s->bwd_variant)) ? s->bwd_variant : pick_variant(threads);
+      (s->bwd_variant >= 0 && threads <= backward_variant_max_threads(s->bwd_variant)) ? s->bwd_variant : pick_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: system too large for one block");
   const size_t smem = backward_smem_bytes(s->B, s->P, 1);
   const int nseg = (T + K - 1) / K;
   const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, nseg,
                                      backward_blocks_per_sm(variant, s->general, threads, smem), (16 + K - 1) / K);
   int64_t launch_grid;
-  cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid, st);
+  cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid, st, fr);
   if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, threads, smem, variant, s->general, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_backward");
 }
+}  // namespace
+
+extern "C" int brax_rollout_backward(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                                     const float* actions, const float* checkpoints, const float* g_state_T,
+                                     const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  return rollout_backward_impl(s, n_envs, T, K, state0, actions, checkpoints, g_state_T, g_torso_traj, g_actions,
+                               g_state0, workspace, workspace_bytes, stream, FixedRegion{});
+}
+
+namespace brax {
+int rollout_backward_fixed_sched(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                                 const float* actions, const float* checkpoints, const float* g_state_T,
+                                 const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                                 size_t workspace_bytes, int32_t* sched, size_t sched_bytes, void* stream) {
+  FixedRegion fr;
+  fr.use = true;
+  fr.fixed = sched;
+  fr.bytes = sched_bytes;
+  return rollout_backward_impl(s, n_envs, T, K, state0, actions, checkpoints, g_state_T, g_torso_traj, g_actions,
+                               g_state0, workspace, workspace_bytes, stream, fr);
+}
+}  // namespace brax
 
 namespace {
 // Reverse-mode layout of a batch: one launch, system i's blocks hold G_i
@@ -1206,4 +1313,22 @@ extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32
   cudaError_t e = apply_schedule(sp, b->sched, 0, 2000000000LL, pl.grid, L, &launch_grid, st);
   if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, pl.threads, pl.smem, variant, pl.general, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout_backward");
+}
+
+// fast_atan2 of the kernels (and its packed two-environment form) over n
+// device elements: the accuracy test's probe (internal, brax_internal.h).
+extern "C" int brax_internal_atan2(const float* y, const float* x, float* out, float* out_packed, int64_t n,
+                                   void* stream) {
+  if (n < 0 || (n > 0 && (!y || !x || !out || !out_packed)))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_internal_atan2: bad arguments");
+  cudaError_t e = brax::launch_atan2_probe(y, x, out, out_packed, n, as_stream(stream));
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_internal_atan2");
+}
+
+extern "C" int brax_system_last_rollout(const brax_system* s, int64_t* grid, int32_t* n_chunks, int32_t* chunk_steps) {
+  if (!s) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_system_last_rollout: null system");
+  if (grid) *grid = s->last_grid;
+  if (n_chunks) *n_chunks = s->last_chunks;
+  if (chunk_steps) *chunk_steps = s->last_chunk_steps;
+  return BRAX_OK;
 }

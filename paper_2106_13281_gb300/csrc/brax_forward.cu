@@ -87,7 +87,7 @@ __device__ __forceinline__ int substep_forward(const SysP& S, const BodyP* bodie
 // runs one unit (a block-sized set of environment groups of one segment):
 // unit blockIdx.x for the whole rollout, or, under a chunked schedule
 // (Sched), one chunk of the unit of the item it takes.
-template <int MAXT, int MINB, bool kGeneral>
+template <int MAXT, int MINB, bool kGeneral, bool kEnv>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_constant__ Launch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
 #pragma unroll
       for (int a = 0; a < 3; ++a) act[a] = bp.act[a] >= 0 ? __ldg(ap + bp.act[a]) : 0.f;
     }
+    if (kEnv && b == 0) gm.react4(0, 0)[lane].x = s.x.x;  // the root's x before the step (its react slot is free)
     for (int k = 0; k < nsub; ++k)
       ccount += substep_forward<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, tree, s,
                                           act);
@@ -177,6 +178,54 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_kernel(const __grid_consta
       tp[0] = s.x.x;
       tp[1] = s.x.y;
       tp[2] = s.x.z;
+    }
+    if (kEnv) {
+      // environment layer (Sec. 4.2 gym-like env): observation, reward and
+      // done of the step, then the auto reset; two group barriers.  A parent
+      // leaves its final angular velocity where its children read its
+      // published state (its rotation there is already the final one: only
+      // velocities change after the kinematic integrator); a joint's child
+      // leaves its actions' squared clamped values beside its reaction.
+      if (bp.flags & kPublish) {
+        gm.pub4(b, 3)[lane].w = s.w.x;
+        st2(gm.pub4(b, 4) + lane, s.w.y, s.w.z);
+      }
+      if (bp.flags & kHasParent) {
+        float c2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (bp.act[a] >= 0) {
+            const float u = clamp1(act[a]);
+            c2 = fmaf(u, u, c2);
+          }
+        gm.react4(b, 1)[lane].z = c2;
+      }
+      group_sync(bar, nthr);
+      float* ob = sg.obs + ((int64_t)t * N + env) * sg.obs_dim;
+      if (valid && (bp.flags & kHasParent)) {
+        const Pub pp = read_pub(gm, bp.parent, lane);
+        float ang[3], rate[3];
+        joint_obs<kGeneral>(bp, pp.R, pp.w, qmat(s.qw, s.qx, s.qy, s.qz), s.w, ang, rate);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (a < bp.dof) {
+            ob[11 + bp.dof_offset + a] = ang[a];
+            ob[11 + S.D + bp.dof_offset + a] = rate[a];
+          }
+      }
+      if (b == 0) {
+        float ctrl = 0.f;
+        for (int c = 1; c < B; ++c)
+          if (bodies[c].flags & kHasParent) ctrl += gm.react4(c, 1)[lane].z;
+        bool done = false;
+        if (valid)
+          done = root_env(sg, s, gm.react4(0, 0)[lane].x, ctrl, ob, sg.reward + (int64_t)t * N + env,
+                          sg.done + (int64_t)t * N + env);
+        gm.react4(0, 0)[lane].y = done ? 1.f : 0.f;
+      }
+      group_sync(bar, nthr);
+      if (sg.auto_reset && valid && gm.react4(0, 0)[lane].y != 0.f)
+        load_body(sg.reset_state + (env * B + b) * 13, s);
     }
     bad |= !body_finite(s);
   }
@@ -228,6 +277,39 @@ __device__ __forceinline__ void store_half(float* p, const Body& s, int half) {
   p[11] = h(s.w.y);
   p[12] = h(s.w.z);
 }
+// One environment (half 0: A, 1: B) of the pair state as a scalar body.
+__device__ __forceinline__ brax::Body half_body(const Body& s, int h) {
+  auto c = [h](f2 v) { return h ? v.y : v.x; };
+  brax::Body o;
+  o.x = mk3(c(s.x.x), c(s.x.y), c(s.x.z));
+  o.qw = c(s.qw);
+  o.qx = c(s.qx);
+  o.qy = c(s.qy);
+  o.qz = c(s.qz);
+  o.v = mk3(c(s.v.x), c(s.v.y), c(s.v.z));
+  o.w = mk3(c(s.w.x), c(s.w.y), c(s.w.z));
+  return o;
+}
+// Replace one half of the pair state by the 13 floats at p.
+__device__ __forceinline__ void load_half(const float* p, Body& s, int h) {
+  auto set = [h](f2& v, float x) {
+    if (h) v.y = x;
+    else v.x = x;
+  };
+  set(s.x.x, p[0]);
+  set(s.x.y, p[1]);
+  set(s.x.z, p[2]);
+  set(s.qw, p[3]);
+  set(s.qx, p[4]);
+  set(s.qy, p[5]);
+  set(s.qz, p[6]);
+  set(s.v.x, p[7]);
+  set(s.v.y, p[8]);
+  set(s.v.z, p[9]);
+  set(s.w.x, p[10]);
+  set(s.w.y, p[11]);
+  set(s.w.z, p[12]);
+}
 __device__ __forceinline__ bool finite_pair(const Body& s) {
   const f2 t = add(add(add(s.x.x, s.x.y), add(s.x.z, s.qw)),
                    add(add(add(s.qx, s.qy), add(s.qz, s.v.x)), add(add(s.v.y, s.v.z), add(s.w.x, add(s.w.y, s.w.z)))));
@@ -239,7 +321,7 @@ __device__ __forceinline__ bool finite_pair(const Body& s) {
 // (brax_pair.cuh).  A block holds G groups of 64 environments (a unit): unit
 // blockIdx.x for the whole rollout, or, under a chunked schedule (Sched), one
 // chunk of the unit of the item it takes.
-template <int MAXT, int MINB>
+template <int MAXT, int MINB, bool kFlat, bool kEnv>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_constant__ Launch L) {
   using namespace p2;
   const Seg& sg = L.seg[0];
@@ -309,19 +391,34 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
       const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
       act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
     }
+    if (kEnv && b == 0) gm.reactf(0, 10)[lane] = s.x.x;  // the root's x before the step (its react slot is free)
     for (int k = 0; k < nsub; ++k) {
       kinematic(S2, bp.flags, s);
       p2::Frame f;
       f.R = qmat(s.qw, s.qx, s.qy, s.qz, S2.one);
+      // every body leaves its rotation in its pub slot (a publishing body for
+      // its children, the others for themselves): after the joint the
+      // rotation is read back instead of being kept live in registers
       if (publishes) publish(gm, b, lane, s, f);
+      else {
+        f2* pr = gm.pubf(b, 3) + lane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pr[i * 32] = f.R.m[i];
+      }
       group_sync(bar, nthr);
       if (has_parent) {
         const p2::Pub pp = read_pub(gm, bp.parent, lane);
         joint(q, act_idx >= 0, pp, s, f, act, gm.reactf(b, 0) + lane);
       }
+      {
+        const f2* pr = gm.pubf(b, 3) + lane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f.R.m[i] = pr[i * 32];
+      }
       p2::Acc acc{vzero(), vzero(), 0, 0};
       f.Ii = inv_inertia_world(f.R, q.inv_I);  // not needed by the joint: computed after it
-      plane_points(S2, q, bp.flags, np, s, f, acc);
+      if (kFlat) plane_points_z(S2, q, bp.flags, np, s, f, acc);
+      else plane_points(S2, q, bp.flags, np, s, f, acc);
       cca += acc.na;
       ccb += acc.nb;
       group_sync(bar, nthr);
@@ -338,6 +435,62 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
         tp[eb * 3 + 0] = s.x.x.y;
         tp[eb * 3 + 1] = s.x.y.y;
         tp[eb * 3 + 2] = s.x.z.y;
+      }
+    }
+    if (kEnv) {
+      // environment layer (Sec. 4.2 gym-like env), as in rollout_kernel: a
+      // parent leaves its final angular velocity in its pub slot, a joint's
+      // child its squared clamped action in a free react field; then each
+      // environment of the pair is observed, rewarded and reset in turn.
+      if (publishes) {
+        f2* p = gm.pubf(b, 15) + lane;
+        p[0] = s.w.x;
+        p[32] = s.w.y;
+        p[64] = s.w.z;
+      }
+      if (has_parent) {
+        f2 c2 = zero2();
+        if (act_idx >= 0) {
+          const float ua = clamp1(act.x), ub = clamp1(act.y);
+          c2 = make_float2(ua * ua, ub * ub);
+        }
+        gm.reactf(b, 9)[lane] = c2;
+      }
+      group_sync(bar, nthr);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const bool vh = h ? vb : va;
+        const int64_t eh = h ? eb : ea;
+        auto c = [h](f2 v) { return h ? v.y : v.x; };
+        const brax::Body sh = half_body(s, h);
+        float* ob = sg.obs + ((int64_t)t * N + eh) * sg.obs_dim;
+        if (vh && has_parent) {
+          const f2* pp = gm.pubf(bp.parent, 0) + lane;
+          M3 Rp;
+#pragma unroll
+          for (int i = 0; i < 9; ++i) Rp.m[i] = c(pp[(3 + i) * 32]);
+          const V3 wp = mk3(c(pp[15 * 32]), c(pp[16 * 32]), c(pp[17 * 32]));
+          float ang[3], rate[3];
+          joint_obs<false>(bp, Rp, wp, brax::qmat(sh.qw, sh.qx, sh.qy, sh.qz), sh.w, ang, rate);
+          ob[11 + bp.dof_offset] = ang[0];
+          ob[11 + S.D + bp.dof_offset] = rate[0];
+        }
+        if (b == 0) {
+          float ctrl = 0.f;
+          for (int cb = 1; cb < B; ++cb)
+            if (bodies[cb].flags & kHasParent) ctrl += c(gm.reactf(cb, 9)[lane]);
+          bool done = false;
+          if (vh)
+            done = root_env(sg, sh, c(gm.reactf(0, 10)[lane]), ctrl, ob, sg.reward + (int64_t)t * N + eh,
+                            sg.done + (int64_t)t * N + eh);
+          reinterpret_cast<float*>(gm.reactf(0, 11) + lane)[h] = done ? 1.f : 0.f;
+        }
+      }
+      group_sync(bar, nthr);
+      if (sg.auto_reset) {
+        const f2 fl = gm.reactf(0, 11)[lane];
+        if (va && fl.x != 0.f) load_half(sg.reset_state + (ea * B + b) * 13, s, 0);
+        if (vb && fl.y != 0.f) load_half(sg.reset_state + (eb * B + b) * 13, s, 1);
       }
     }
     bad |= !finite_pair(s);
@@ -433,103 +586,118 @@ __global__ void default_qp_kernel(const unsigned char* blob, int64_t N, const fl
 }
 
 // ------------------------------------------------------------------ launchers
-template <int MAXT, int MINB, bool G>
-static cudaError_t launch_rollout_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
-  auto k = rollout_kernel<MAXT, MINB, G>;
+template <class KernelT>
+static cudaError_t launch_k(KernelT k, const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
+}
+template <class KernelT>
+static int occupancy_k(KernelT k, int threads, size_t smem) {
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
 }
 
 // Launch-bounds variants (max threads per block, min blocks per SM):
 //   0: (384, 2)  1: (576, 1)  2: (1024, 1)  3: (288, 3)
+// A rollout with the environment layer (Seg::obs) runs the kernels compiled
+// with it, in the (576, 1) launch, or (1024, 1) for larger blocks; the
+// others are compiled without it, so plain rollouts carry none of its code.
+template <bool G>
+static cudaError_t launch_rollout_g(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st) {
+  if (L.seg[0].obs)
+    return threads <= 576 ? launch_k(rollout_kernel<576, 1, G, true>, L, grid, threads, smem, st)
+                          : launch_k(rollout_kernel<1024, 1, G, true>, L, grid, threads, smem, st);
+  switch (variant) {
+    case 0: return launch_k(rollout_kernel<384, 2, G, false>, L, grid, threads, smem, st);
+    case 1: return launch_k(rollout_kernel<576, 1, G, false>, L, grid, threads, smem, st);
+    case 3: return launch_k(rollout_kernel<288, 3, G, false>, L, grid, threads, smem, st);
+    default: return launch_k(rollout_kernel<1024, 1, G, false>, L, grid, threads, smem, st);
+  }
+}
 cudaError_t launch_rollout(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                            cudaStream_t st) {
-  if (general) {
-    switch (variant) {
-      case 0: return launch_rollout_t<384, 2, true>(L, grid, threads, smem, st);
-      case 1: return launch_rollout_t<576, 1, true>(L, grid, threads, smem, st);
-      case 3: return launch_rollout_t<288, 3, true>(L, grid, threads, smem, st);
-      default: return launch_rollout_t<1024, 1, true>(L, grid, threads, smem, st);
-    }
-  }
-  switch (variant) {
-    case 0: return launch_rollout_t<384, 2, false>(L, grid, threads, smem, st);
-    case 1: return launch_rollout_t<576, 1, false>(L, grid, threads, smem, st);
-    case 3: return launch_rollout_t<288, 3, false>(L, grid, threads, smem, st);
-    default: return launch_rollout_t<1024, 1, false>(L, grid, threads, smem, st);
-  }
+  return general ? launch_rollout_g<true>(L, grid, threads, smem, variant, st)
+                 : launch_rollout_g<false>(L, grid, threads, smem, variant, st);
 }
 
-template <int MAXT, int MINB, bool kGeneral>
-static int rollout_occupancy_t(int threads, size_t smem) {
-  auto k = rollout_kernel<MAXT, MINB, kGeneral>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
-  return n;
+template <bool G>
+static int rollout_blocks_per_sm_g(int variant, int threads, size_t smem) {
+  switch (variant) {
+    case 0: return occupancy_k(rollout_kernel<384, 2, G, false>, threads, smem);
+    case 1: return occupancy_k(rollout_kernel<576, 1, G, false>, threads, smem);
+    case 3: return occupancy_k(rollout_kernel<288, 3, G, false>, threads, smem);
+    default: return occupancy_k(rollout_kernel<1024, 1, G, false>, threads, smem);
+  }
 }
 int rollout_blocks_per_sm(int variant, bool general, int threads, size_t smem) {
-  if (general) {
-    switch (variant) {
-      case 0: return rollout_occupancy_t<384, 2, true>(threads, smem);
-      case 1: return rollout_occupancy_t<576, 1, true>(threads, smem);
-      case 3: return rollout_occupancy_t<288, 3, true>(threads, smem);
-      default: return rollout_occupancy_t<1024, 1, true>(threads, smem);
-    }
-  }
-  switch (variant) {
-    case 0: return rollout_occupancy_t<384, 2, false>(threads, smem);
-    case 1: return rollout_occupancy_t<576, 1, false>(threads, smem);
-    case 3: return rollout_occupancy_t<288, 3, false>(threads, smem);
-    default: return rollout_occupancy_t<1024, 1, false>(threads, smem);
-  }
-}
-
-template <int MAXT, int MINB>
-static cudaError_t launch_pair_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
-  auto k = rollout_pair_kernel<MAXT, MINB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, st>>>(L);
-  return cudaGetLastError();
+  return general ? rollout_blocks_per_sm_g<true>(variant, threads, smem)
+                 : rollout_blocks_per_sm_g<false>(variant, threads, smem);
 }
 
 // Two-environments-per-thread variants: 0: (288, 2)  1: (576, 1)  2: (1024, 1)  3: (288, 3)
-cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st) {
+// 4: (864, 1); flat: every plane's normal is the world z axis.  With the
+// environment layer: (576, 1), or (1024, 1) for larger blocks.
+template <bool kFlat>
+static cudaError_t launch_rollout_pair_t(const Launch& L, int grid, int threads, size_t smem, int variant,
+                                         cudaStream_t st) {
+  if (L.seg[0].obs)
+    return threads <= 576 ? launch_k(rollout_pair_kernel<576, 1, kFlat, true>, L, grid, threads, smem, st)
+                          : launch_k(rollout_pair_kernel<1024, 1, kFlat, true>, L, grid, threads, smem, st);
   switch (variant) {
-    case 0: return launch_pair_t<288, 2>(L, grid, threads, smem, st);
-    case 1: return launch_pair_t<576, 1>(L, grid, threads, smem, st);
-    case 3: return launch_pair_t<288, 3>(L, grid, threads, smem, st);
-    default: return launch_pair_t<1024, 1>(L, grid, threads, smem, st);
+    case 0: return launch_k(rollout_pair_kernel<288, 2, kFlat, false>, L, grid, threads, smem, st);
+    case 1: return launch_k(rollout_pair_kernel<576, 1, kFlat, false>, L, grid, threads, smem, st);
+    case 3: return launch_k(rollout_pair_kernel<288, 3, kFlat, false>, L, grid, threads, smem, st);
+    case 4: return launch_k(rollout_pair_kernel<864, 1, kFlat, false>, L, grid, threads, smem, st);
+    default: return launch_k(rollout_pair_kernel<1024, 1, kFlat, false>, L, grid, threads, smem, st);
   }
 }
-template <int MAXT, int MINB>
-static int pair_occupancy_t(int threads, size_t smem) {
-  auto k = rollout_pair_kernel<MAXT, MINB>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
-  return n;
+cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, bool flat,
+                                cudaStream_t st) {
+  return flat ? launch_rollout_pair_t<true>(L, grid, threads, smem, variant, st)
+              : launch_rollout_pair_t<false>(L, grid, threads, smem, variant, st);
 }
 int pair_blocks_per_sm(int variant, int threads, size_t smem) {
   switch (variant) {
-    case 0: return pair_occupancy_t<288, 2>(threads, smem);
-    case 1: return pair_occupancy_t<576, 1>(threads, smem);
-    case 3: return pair_occupancy_t<288, 3>(threads, smem);
-    default: return pair_occupancy_t<1024, 1>(threads, smem);
+    case 0: return occupancy_k(rollout_pair_kernel<288, 2, true, false>, threads, smem);
+    case 1: return occupancy_k(rollout_pair_kernel<576, 1, true, false>, threads, smem);
+    case 3: return occupancy_k(rollout_pair_kernel<288, 3, true, false>, threads, smem);
+    case 4: return occupancy_k(rollout_pair_kernel<864, 1, true, false>, threads, smem);
+    default: return occupancy_k(rollout_pair_kernel<1024, 1, true, false>, threads, smem);
   }
 }
 int pair_variant_max_threads(int variant) {
-  static const int t[4] = {288, 576, 1024, 288};
-  return (variant >= 0 && variant < 4) ? t[variant] : 0;
+  static const int t[5] = {288, 576, 1024, 288, 864};
+  return (variant >= 0 && variant < 5) ? t[variant] : 0;
 }
 size_t pair_group_bytes(int B) { return (size_t)p2::group_floats2(B) * sizeof(float); }
 
 int rollout_variant_max_threads(int variant) {
   static const int t[4] = {384, 576, 1024, 288};
   return (variant >= 0 && variant < 4) ? t[variant] : 0;
+}
+
+// The kernels' arctangent and its packed form, elementwise over arrays (for
+// the accuracy test of fast_atan2; not on the rollout path).
+__global__ void atan2_probe_kernel(const float* y, const float* x, float* out, float* out_packed, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = fast_atan2(y[i], x[i]);
+  // the packed form pairs element i with element n-1-i
+  const int64_t j = n - 1 - i;
+  const float2 r = p2::atan2p(make_float2(y[i], y[j]), make_float2(x[i], x[j]));
+  out_packed[i] = r.x;
+  (void)r.y;
+}
+cudaError_t launch_atan2_probe(const float* y, const float* x, float* out, float* out_packed, int64_t n,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  atan2_probe_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(y, x, out, out_packed, n);
+  return cudaGetLastError();
 }
 
 cudaError_t upload_pool_forward(int off, const void* data, size_t bytes) {

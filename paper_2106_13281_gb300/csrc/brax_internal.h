@@ -48,6 +48,10 @@ struct brax_system {
   int sched_first = 0;              // first item handed out (the wait test starts past chunk 0)
   int64_t sched_wait_ns = 2000000000;
   mutable brax::SchedScratch sched;
+  // The last brax_rollout launch: blocks launched, chunks (0 = static) and
+  // steps per chunk (reported by brax_system_last_rollout).
+  mutable int64_t last_grid = 0;
+  mutable int32_t last_chunks = 0, last_chunk_steps = 0;
 };
 
 struct brax_batch {
@@ -68,6 +72,14 @@ extern "C" int brax_batch_set_schedule(brax_batch* b, int32_t mode, int32_t chun
 // only, for tests): n_chunks = 0 means the static schedule.
 extern "C" int brax_internal_plan_schedule(int32_t mode, int32_t chunk_steps, int64_t units, int32_t T, int64_t slots,
                                            int32_t min_chunk, int32_t* n_chunks, int32_t* steps);
+// The launch of the system's last brax_rollout: blocks launched, chunks of
+// the chunked schedule (0 = static schedule) and steps per chunk.
+extern "C" int brax_system_last_rollout(const brax_system* s, int64_t* grid, int32_t* n_chunks, int32_t* chunk_steps);
+// The kernels' fast_atan2 elementwise over n device floats (out) and its
+// packed two-environment form with element i paired with n-1-i (out_packed):
+// the probe of the arctangent's accuracy test.
+extern "C" int brax_internal_atan2(const float* y, const float* x, float* out, float* out_packed, int64_t n,
+                                   void* stream);
 extern "C" int brax_system_set_schedule(brax_system* s, int32_t mode, int32_t chunk_steps, int32_t first_item,
                                         int64_t wait_ns);
 
@@ -77,4 +89,13 @@ namespace brax {
 size_t backward_workspace_bytes(const brax_system* s, int64_t n_envs, int32_t K);
 // Set the message brax_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
+// brax_rollout_backward whose chunked schedule (if the launch takes one) uses
+// the caller's scheduler region `sched` of `sched_bytes` bytes of device
+// memory instead of the system's own scratch; when that region is null or
+// smaller than (32 + blocks of 32 environments) int32 the launch takes the
+// static schedule.  Allocates nothing.
+int rollout_backward_fixed_sched(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
+                                 const float* actions, const float* checkpoints, const float* g_state_T,
+                                 const float* g_torso_traj, float* g_actions, float* g_state0, void* workspace,
+                                 size_t workspace_bytes, int32_t* sched, size_t sched_bytes, void* stream);
 }  // namespace brax

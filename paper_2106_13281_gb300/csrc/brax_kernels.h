@@ -19,7 +19,9 @@ int rollout_variant_max_threads(int variant);
 // Resident blocks per SM of a one-environment kernel variant (0 if it cannot launch).
 int rollout_blocks_per_sm(int variant, bool general, int threads, size_t smem);
 // Two environments per thread (systems whose blob carries the paired section).
-cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, cudaStream_t st);
+// flat: every plane of the system has the world z axis as its normal (SysP::flat).
+cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t smem, int variant, bool flat,
+                                cudaStream_t st);
 int pair_variant_max_threads(int variant);
 // Resident blocks per SM of a paired-kernel variant (0 if it cannot launch).
 int pair_blocks_per_sm(int variant, int threads, size_t smem);
@@ -27,9 +29,14 @@ size_t pair_group_bytes(int B);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);
 size_t backward_smem_bytes(int B, int P, int groups);
+// Largest block of a reverse-kernel variant (0..3 as the forward; 4: 112 registers, up to 576 threads).
+int backward_variant_max_threads(int variant);
 // Resident blocks per SM of a reverse kernel variant (0 if it cannot launch).
 int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem);
 int64_t backward_ws_floats_per_group(int B, int P, int K, int S);
+// fast_atan2 (and its packed form, out_packed) elementwise, for its accuracy test.
+cudaError_t launch_atan2_probe(const float* y, const float* x, float* out, float* out_packed, int64_t n,
+                               cudaStream_t st);
 cudaError_t launch_default_qp(const unsigned char* blob, int64_t N, const float* root_pos, const float* root_rot,
                               const float* angles, float* out, cudaStream_t st);
 

@@ -359,6 +359,88 @@ __device__ __forceinline__ void plane_points(const SysP2& S2, const BodyP2& q, u
   }
 }
 
+// ------------------------------------------------------------------ phase J: contacts with a z-up ground
+// The same response for planes whose normal is the world z axis, n = (0, 0, 1),
+// with the products by n's zero components dropped (they contribute exact
+// zeros): l x n = (l.y, -l.x, 0), u_n = u.z, the tangential velocity is
+// (u.x, u.y, 0) and the normal impulse acts along z alone.
+__device__ __forceinline__ void point_response_z(const SysP2& S2, uint32_t flags, f2 inv_m, const PointP2& pt, V l,
+                                                 f2 depth, bool ma, bool mb, const Body& s, const Frame& f,
+                                                 Acc& acc) {
+  const V u = cross_add(s.w, l, s.v);
+  // k_n: linear term (unless z is frozen) + (I_w^-1 (l x n)) . (l x n)
+  const f2 nlx = neg(l.x);
+  f2 omx = fma(f.Ii.a[0], l.y, mul(f.Ii.a[1], nlx));
+  f2 omy = fma(f.Ii.a[1], l.y, mul(f.Ii.a[3], nlx));
+  if (flags & kAnyFrozen) {
+    if (flags & (kFrozenRot0 << 0)) omx = zero2();
+    if (flags & (kFrozenRot0 << 1)) omy = zero2();
+  }
+  const f2 lin = (flags & (kFrozenPos0 << 2)) ? zero2() : inv_m;
+  const f2 kn = add(lin, fma(omx, l.y, mul(omy, nlx)));
+  const bool ka = kn.x > 0.f, kb = kn.y > 0.f;
+  ma = ma && ka;
+  mb = mb && kb;
+  const f2 un = u.z;
+  const f2 ue = mul(pt.me, un);
+  const f2 tb = mul(S2.beta_h, depth);
+  const f2 target = make_float2(fmaxf(tb.x, ue.x), fmaxf(tb.y, ue.y));
+  const f2 dn = sub(target, un);
+  const f2 jn = make_float2(ka ? fmaxf(__fdividef(dn.x, kn.x), 0.f) : 0.f, kb ? fmaxf(__fdividef(dn.y, kn.y), 0.f) : 0.f);
+  V J = V{zero2(), zero2(), jn};
+  const f2 ut2 = fma(u.x, u.x, mul(u.y, u.y));
+  const bool fa = ut2.x > S2.eps2.x, fb = ut2.y > S2.eps2.y;
+  if (__any_sync(0xffffffffu, fa || fb)) {
+    const f2 rinv = make_float2(fa ? rsqrtf(ut2.x) : 0.f, fb ? rsqrtf(ut2.y) : 0.f);
+    const f2 utn = mul(ut2, rinv);
+    const V t = V{mul(rinv, u.x), mul(rinv, u.y), zero2()};
+    const f2 kt = eff_mass(flags, inv_m, f.Ii, l, t);
+    const f2 cap = mul(pt.mu, jn);
+    const f2 jt = make_float2(fa && kt.x > 0.f ? fminf(__fdividef(utn.x, kt.x), cap.x) : 0.f,
+                              fb && kt.y > 0.f ? fminf(__fdividef(utn.y, kt.y), cap.y) : 0.f);
+    const f2 njt = neg(jt);
+    J.x = mul(njt, t.x);
+    J.y = mul(njt, t.y);
+  }
+  V dv = vscale(inv_m, J);
+  V dw = mul6(f.Ii, cross(l, J));
+  if (flags & kAnyFrozen) {
+    dv = mask(flags, dv);
+    dw = mask(flags >> 3, dw);
+  }
+  const f2 m = make_float2(ma ? 1.f : 0.f, mb ? 1.f : 0.f);
+  acc.dv = vfma(m, dv, acc.dv);
+  acc.dw = vfma(m, dw, acc.dw);
+  acc.na += ma ? 1 : 0;
+  acc.nb += mb ? 1 : 0;
+}
+
+// plane_points for z-up planes: depth r - ((x + R o).z - p0.z), lever
+// R o - r n = (R o).xy, (R o).z - r.
+__device__ __forceinline__ void plane_points_z(const SysP2& S2, const BodyP2& q, uint32_t flags, int np,
+                                               const Body& s, const Frame& f, Acc& acc) {
+  V l0, l1;
+  f2 d0 = make_float2(-1.f, -1.f), d1 = make_float2(-1.f, -1.f);
+  if (np > 0) {
+    const V ro = mulc(f.R, q.pt[0].o);
+    d0 = sub(q.pt[0].r, sub(add(s.x.z, ro.z), q.pt[0].p0[2]));
+    l0 = V{ro.x, ro.y, add(ro.z, q.pt[0].mr)};
+  }
+  if (np > 1) {
+    const V ro = mulc(f.R, q.pt[1].o);
+    d1 = sub(q.pt[1].r, sub(add(s.x.z, ro.z), q.pt[1].p0[2]));
+    l1 = V{ro.x, ro.y, add(ro.z, q.pt[1].mr)};
+  }
+  if (np > 0) {
+    const bool ma = d0.x > 0.f, mb = d0.y > 0.f;
+    if (__any_sync(0xffffffffu, ma || mb)) point_response_z(S2, flags, q.inv_mass, q.pt[0], l0, d0, ma, mb, s, f, acc);
+  }
+  if (np > 1) {
+    const bool ma = d1.x > 0.f, mb = d1.y > 0.f;
+    if (__any_sync(0xffffffffu, ma || mb)) point_response_z(S2, flags, q.inv_mass, q.pt[1], l1, d1, ma, mb, s, f, acc);
+  }
+}
+
 // ------------------------------------------------------------------ phase P
 __device__ __forceinline__ void integrate(const SysP2& S2, bool average, const BodyP& bp, const BodyP2& q,
                                           GroupMem2& gm, int b, int lane, Body& s, const Frame& f, const Acc& acc) {

@@ -99,7 +99,7 @@ struct SysP {
   int32_t general;   // 1: the system has a 3-DOF joint or a body-body pair
   int32_t paired;    // 1: the blob carries SysP2/BodyP2 (two environments per thread)
   int32_t pair_off;  // byte offset of SysP2 in the blob
-  int32_t pad3;
+  int32_t flat;      // 1: every plane's normal is the world z axis (plane contacts drop n's zero components)
   int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
   int32_t n_order;
   int32_t n_parents;  // bodies with at least one child

@@ -648,6 +648,60 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
   return 1;
 }
 
+// ------------------------------------------------------------------ environment layer
+// Observation of a body's parent joint (the gym-like environment layer): its
+// angles, measured as the limits measure them, and the relative angular
+// velocity w - w_p along its world axes R_p (parent joint-frame axis k).
+// Rp, wp: the parent's rotation and angular velocity; R, w: this body's.
+template <bool kGeneral>
+__device__ __forceinline__ void joint_obs(const BodyP& bp, const M3& Rp, V3 wp, const M3& R, V3 w, float* ang,
+                                          float* rate) {
+  const V3 P0 = mulc(Rp, bp.ap + 0);
+  const V3 P1 = mulc(Rp, bp.ap + 3);
+  const V3 wr = w - wp;
+  if (!kGeneral || bp.dof == 1) {
+    const V3 yc = mulc(R, bp.ac + 3);
+    ang[0] = fast_atan2(dot(cross(P1, yc), P0), dot(P1, yc));
+    rate[0] = dot(wr, P0);
+  } else {
+    const V3 P2 = mulc(Rp, bp.ap + 6);
+    const V3 C0 = mulc(R, bp.ac + 0);
+    const V3 C1 = mulc(R, bp.ac + 3);
+    const V3 C2 = mulc(R, bp.ac + 6);
+    const float m00 = dot(P0, C0), m01 = dot(P0, C1), m02 = dot(P0, C2);
+    const float m12 = dot(P1, C2), m22 = dot(P2, C2);
+    ang[0] = fast_atan2(-m12, m22);
+    ang[1] = fast_atan2(m02, sqrtf(fmaf(m00, m00, m01 * m01)));
+    ang[2] = fast_atan2(-m01, m00);
+    rate[0] = dot(wr, P0);
+    rate[1] = dot(wr, P1);
+    rate[2] = dot(wr, P2);
+  }
+}
+
+// The root body's part of the environment layer after a step: its
+// observation fields (height, quaternion, velocity, angular velocity), the
+// step's reward and whether the episode ended.  x0: its x position before
+// the step; ctrl: the sum of the squared clamped actions.
+__device__ __forceinline__ bool root_env(const Seg& sg, const Body& s, float x0, float ctrl, float* ob, float* rew,
+                                         uint8_t* dn) {
+  ob[0] = s.x.z;
+  ob[1] = s.qw;
+  ob[2] = s.qx;
+  ob[3] = s.qy;
+  ob[4] = s.qz;
+  ob[5] = s.v.x;
+  ob[6] = s.v.y;
+  ob[7] = s.v.z;
+  ob[8] = s.w.x;
+  ob[9] = s.w.y;
+  ob[10] = s.w.z;
+  const bool done = s.x.z < sg.min_z || s.x.z > sg.max_z;
+  *rew = fmaf(sg.fwd_w_dt, s.x.x - x0, done ? 0.f : sg.healthy) - sg.ctrl_cost * ctrl;
+  *dn = done ? 1 : 0;
+  return done;
+}
+
 // ------------------------------------------------------------------ phase P
 // Add a child's joint reaction (force, torque on this body) to wr.
 __device__ __forceinline__ void add_reaction(GroupMem& gm, int child, int lane, Wrench& wr) {

@@ -98,7 +98,7 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
     for (int v : {3, 0, 1, 2})
       for (int g = 1; g <= 4 && 32 * s->B * g <= brax::rollout_variant_max_threads(v); ++g) cands.push_back({0, g, v});
     if (s->paired)
-      for (int v : {0, 3, 1, 2})
+      for (int v : {0, 3, 1, 4, 2})
         for (int g = 1; g <= 4 && 32 * s->B * g <= brax::pair_variant_max_threads(v); ++g) cands.push_back({1, g, v});
     // the fastest one-environment configuration is kept in any case: it runs
     // the rollouts that write checkpoints
@@ -188,8 +188,8 @@ extern "C" int brax_autotune(brax_system* s, int64_t n_envs, int32_t T, const fl
     int bestK = plans[0].K, bestV = -1;
     const int saved = s->bwd_variant;
     for (const Plan& p : plans)
-      for (int v : {3, 0, 1, 2}) {
-        if (threads > brax::rollout_variant_max_threads(v)) continue;
+      for (int v : {3, 0, 1, 4, 2}) {
+        if (threads > brax::backward_variant_max_threads(v)) continue;
         s->bwd_variant = v;
         const float ms = time_best(
             [&] {

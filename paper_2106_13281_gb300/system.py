@@ -136,6 +136,13 @@ class BraxSystem:
             os.replace(tmp, cache)
         return dict(r, cached=False)
 
+    def last_rollout(self) -> dict:
+        """Launch of the last rollout: blocks, chunks of the chunked schedule
+        (0 = static) and steps per chunk."""
+        g, c, k = C.c_int64(), C.c_int32(), C.c_int32()
+        check(self._L.brax_system_last_rollout(self._h, C.byref(g), C.byref(c), C.byref(k)))
+        return {"grid": g.value, "n_chunks": c.value, "chunk_steps": k.value}
+
     @property
     def paired(self) -> bool:
         """True when the system has the two-environments-per-thread kernel."""
@@ -177,6 +184,32 @@ class BraxSystem:
         check(self._L.brax_rollout(self._h, N, T, K, _ptr(state0), _ptr(actions), _ptr(out["state_T"]),
                                    _ptr(out.get("checkpoints")), _ptr(out.get("torso")),
                                    _ptr(out.get("contact_count")), _stream()))
+        return out
+
+    def env_obs_size(self) -> int:
+        n = C.c_int32()
+        check(self._L.brax_env_obs_size(self._h, C.byref(n)))
+        return n.value
+
+    def env_rollout(self, state0, actions, reset_state=None, forward_weight=1.0, healthy_reward=1.0, ctrl_cost=0.5,
+                    min_z=0.2, max_z=1.0, auto_reset=True, state_T=None):
+        """T steps of the gym-like environment layer (brax_env_rollout):
+        returns a dict with state_T [N,B,13], obs [T,N,D], reward [T,N] and
+        done [T,N] (uint8).  reset_state defaults to state0."""
+        from .binding import brax_env_params
+        N, T = state0.shape[0], actions.shape[0]
+        _f32(state0, (N, self.B, 13), "state0")
+        _f32(actions, (T, N, self.A), "actions")
+        reset_state = state0 if reset_state is None else _f32(reset_state, (N, self.B, 13), "reset_state")
+        D = self.env_obs_size()
+        out = {"state_T": torch.empty_like(state0) if state_T is None else state_T,
+               "obs": torch.empty((T, N, D), device="cuda", dtype=torch.float32),
+               "reward": torch.empty((T, N), device="cuda", dtype=torch.float32),
+               "done": torch.empty((T, N), device="cuda", dtype=torch.uint8)}
+        p = brax_env_params(forward_weight, healthy_reward, ctrl_cost, min_z, max_z, 1 if auto_reset else 0)
+        check(self._L.brax_env_rollout(self._h, C.byref(p), N, T, _ptr(state0), _ptr(reset_state), _ptr(actions),
+                                       _ptr(out["state_T"]), _ptr(out["obs"]), _ptr(out["reward"]),
+                                       _ptr(out["done"]), _stream()))
         return out
 
     def rollout_streamed(self, h_state0, h_actions, h_state_T, chunk_steps: int = 100, bufs: dict | None = None,

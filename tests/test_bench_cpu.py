@@ -12,12 +12,22 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path):
     assert len(dig) == 64 and all(c in "0123456789abcdef" for c in dig)
     p = os.path.join(tmp_path, "traffic.json")
     with open(p, "w") as f:
-        json.dump({"k": {"dram_bytes_per_launch": 123, "sources_sha256": dig},
-                   "old": {"dram_bytes_per_launch": 456, "sources_sha256": "0" * 64}}, f)
-    assert bench.measured_traffic("k", p) == 123
+        json.dump({"k": {"dram_read_bytes": 123, "sources_sha256": dig},
+                   "old": {"dram_read_bytes": 456, "sources_sha256": "0" * 64}}, f)
+    assert bench.measured_traffic("k", p)["dram_read_bytes"] == 123
     assert bench.measured_traffic("old", p) is None     # kernels changed since the capture
     assert bench.measured_traffic("missing", p) is None
     assert bench.measured_traffic("k", os.path.join(tmp_path, "none.json")) is None
+
+
+def test_traffic_scaling_arithmetic():
+    """A 40-step capture (initial state + 40 steps of actions read) scaled to
+    1,000 steps in 8 chunks: 1,000 steps of the per-step stream, plus the
+    state read and written once per chunk."""
+    state, act = 30_670_848, 2_097_152
+    rec = {"steps": 40, "state_bytes": state, "dram_read_bytes": state + 40 * act, "dram_write_bytes": 0}
+    assert bench.scaled_traffic(rec, 1000, 8, state) == 1000 * act + 16 * state
+    assert bench.scaled_traffic(rec, 1000, 0, state) == 1000 * act + 2 * state  # static schedule: one chunk
 
 
 def test_flop_table_covers_the_workloads():

@@ -74,12 +74,18 @@ def test_adjoint_matches_oracle_tape(brax, name, drop, T):
     ga_ref, gs_ref = orc.vjp(d, st, a, gT, gtor)
     _, cc_ref = orc.rollout(d, st, a, contact_count=True)
     same = (cc == cc_ref) & decided_envs(d, st, a)
-    assert same.mean() >= 0.7
-    errs_a = [rel_err(ga[:, n], ga_ref[:, n]) for n in range(N) if same[n]]
-    errs_s = [rel_err(gs[n], gs_ref[n]) for n in range(N) if same[n]]
-    assert np.median(errs_a) < 1e-3 and np.median(errs_s) < 1e-3, (np.median(errs_a), np.median(errs_s))
-    assert np.mean(np.array(errs_a) < 1e-3) >= 0.9, sorted(errs_a)[-5:]
-    assert np.mean(np.array(errs_s) < 1e-3) >= 0.9, sorted(errs_s)[-5:]
+    assert same.mean() >= 0.8
+    errs_a = np.array([rel_err(ga[:, n], ga_ref[:, n]) for n in range(N) if same[n]])
+    errs_s = np.array([rel_err(gs[n], gs_ref[n]) for n in range(N) if same[n]])
+    if name != "biped":
+        assert errs_a.max() < 1e-3 and errs_s.max() < 1e-3, (errs_a.max(), errs_s.max())
+    else:
+        # 30 substeps of capsule-capsule contact between 17 bodies amplify the
+        # FP32 rounding of the trajectory; most environments stay within 1e-3
+        # and none leaves 1e-2
+        assert np.mean(errs_a < 1e-3) >= 0.9 and np.mean(errs_s < 1e-3) >= 0.9, (sorted(errs_a)[-5:],
+                                                                                  sorted(errs_s)[-5:])
+        assert errs_a.max() < 1e-2 and errs_s.max() < 1e-2, (errs_a.max(), errs_s.max())
 
 
 @pytest.mark.parametrize("name,drop", [("pendulum", 0.0), ("quadruped", 0.38), ("biped", 0.0), ("arm_box", 0.0),
@@ -154,7 +160,7 @@ def test_adjoint_vs_fp64_central_differences(brax):
                 skipped += 1
                 continue
             g = ga[t, n, k]
-            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-4 * np.abs(ga[:, n]).max(), (t, n, k, fd[n], g)
+            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)), (t, n, k, fd[n], g)
             checked += 1
     assert checked >= 100, (checked, skipped)
     for _ in range(10):
@@ -169,7 +175,7 @@ def test_adjoint_vs_fp64_central_differences(brax):
             if not same[n] or sp_[n] != sig0[n] or sm_[n] != sig0[n]:
                 continue
             g = gs[n, b, j]
-            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-4 * np.abs(gs[n]).max(), (b, j, n, fd[n], g)
+            assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-12, (b, j, n, fd[n], g)
 
 
 def test_checkpoint_interval_does_not_change_gradients(brax):
@@ -279,20 +285,24 @@ def test_reverse_schedule_wait_gives_up_with_timeout_status(brax):
     assert torch.isfinite(ga).all() and torch.isfinite(gs).all()
 
 
-def test_long_rollout_gradients_finite(brax):
-    """1000 steps with checkpoints every 10: the recomputation path runs and
-    the gradients stay finite."""
+def test_long_rollout_recomputation_is_exact(brax):
+    """1000 steps: with checkpoints every 10 steps the reverse pass
+    recomputes every step from its segment's checkpoint, with checkpoints
+    every step it recomputes nothing but the substeps; both give bitwise the
+    same gradients (the forward is deterministic), and they are finite."""
     d = S.quadruped()
     sysm = brax(d)
-    N, T, K = 64, 1000, 10
+    N, T = 64, 1000
     rp, rr, ang = S.initial_conditions(d, N, 3, height_jitter=0.05)
     st = orc.default_qp(d, N, rp, rr, ang)
     a = S.actions(d, N, T, 3)
     gT = np.zeros_like(st)
     gT[:, 0, 0] = -1.0
-    ga, gs, _ = gpu_grad(sysm, st, a, gT, None, K)
+    ga, gs, _ = gpu_grad(sysm, st, a, gT, None, 10)
     assert np.isfinite(ga).all() and np.isfinite(gs).all()
     assert np.abs(ga).max() > 0
+    ga1, gs1, _ = gpu_grad(sysm, st, a, gT, None, 1)
+    assert np.array_equal(ga, ga1) and np.array_equal(gs, gs1)
 
 
 def test_autograd_function(brax):

@@ -1,9 +1,13 @@
 """Parity of the CUDA forward path with the FP64 oracle (GPU).
 
 Inputs are seeded and shared; the oracle runs on the same FP32-rounded
-initial states.  Tolerances: one step <= 1e-5 m in position; 50 steps
-<= 1e-3 m; beyond the chaotic horizon the torso displacement distributions
-agree (two-sample KS test and means within 3 standard errors)."""
+initial states.  Tolerances: one step <= 1e-5 m in position, 1e-4 in the
+quaternion, 2e-4 m/s in velocity (the velocity that moves a body by the
+position tolerance within one 0.05 s step) and 4e-3 rad/s in angular
+velocity (the rate that turns it by the quaternion tolerance within one
+step); 50 steps <= 1e-3 m in every environment; beyond the chaotic horizon
+the torso displacement distributions agree (two-sample KS test and means
+within 3 standard errors)."""
 import math
 
 import numpy as np
@@ -89,6 +93,10 @@ def test_one_step_parity(brax, name, drop):
     assert dpos <= 1e-5, dpos
     dq = np.abs(got[ok][..., 3:7] - ref[ok][..., 3:7]).max()
     assert dq <= 1e-4, dq
+    dv = np.abs(got[ok][..., 7:10] - ref[ok][..., 7:10]).max()
+    assert dv <= 2e-4, dv
+    dw = np.abs(got[ok][..., 10:13] - ref[ok][..., 10:13]).max()
+    assert dw <= 4e-3, dw
     cc = out["contact_count"].cpu().numpy()
     assert cc_ref.sum() > 0 or name == "pendulum"
     if name.startswith("capsule_"):
@@ -110,7 +118,9 @@ def test_step_equals_rollout_of_one(brax):
 
 
 def test_fifty_step_parity_quadruped(brax):
-    """Quadruped, 128 envs: 50 steps within 1e-3 m of the FP64 oracle."""
+    """Quadruped, 128 envs: after 50 steps every body of every environment
+    is within 1e-3 m of the FP64 oracle (no environment excluded; the
+    measured maximum is about 1.3e-5 m)."""
     d = S.quadruped()
     sysm = brax(d)
     N, T = 128, 50
@@ -119,33 +129,43 @@ def test_fifty_step_parity_quadruped(brax):
     ref = orc.rollout(d, st, a.astype(np.float64))
     got = sysm.rollout(cuda(st), cuda(a))["state_T"].cpu().numpy()
     err = np.abs(got[..., 0:3] - ref[..., 0:3]).max(axis=(1, 2))
-    assert np.median(err) <= 1e-3, np.sort(err)[-10:]
-    assert np.mean(err <= 1e-3) >= 0.9, np.sort(err)[-10:]
+    assert err.max() <= 1e-3, np.sort(err)[-10:]
 
 
 def test_full_size_fifty_steps_sampled_parity(brax):
     """The headline size, 65,536 environments, in the launch the bench times
     (two environments per thread, one 64-environment group per block, the
-    automatic chunked schedule: 1,024 blocks are 3.37 resident waves, so 50
-    steps run as chunks of 16, 16, 16 and 2): 96 sampled environments (the
-    first and last of the batch and of a block, the rest at random) within
-    1e-3 m of the FP64 oracle after 50 steps, as at 128 environments."""
+    automatic chunked schedule), 50 steps as five launches of 10 (bitwise one
+    launch of 50): 96 sampled environments (the first and last of the batch
+    and of a block, the rest at random) within 1e-3 m of the FP64 oracle
+    after 50 steps, every one along whose GPU trajectory the oracle takes its
+    own branches (checked window by window from the GPU's state after every
+    10 steps); at least 90 % of them."""
+    from parity_util import branch_consistent_envs
     d = S.quadruped()
     sysm = brax(d)
     sysm.set_pair_launch(1, 1, 0)
-    N, T = 65536, 50
+    N, T, W = 65536, 50, 10
     st, _ = initial(d, N, 0)
     a = S.actions(d, N, T, 0)
-    got = sysm.rollout(cuda(st), cuda(a), contact_count=True)
-    sysm.sync_status()
     idx = np.unique(np.concatenate([[0, 1, 63, 64, N - 1], np.random.default_rng(1).choice(N, 91, replace=False)]))
-    ref = orc.rollout(d, st[idx], a[:, idx].astype(np.float64))
-    g = got["state_T"].cpu().numpy()[idx]
+    cur, gpu_starts = cuda(st), [st[idx]]
+    for w in range(T // W):
+        cur = sysm.rollout(cur, cuda(a[w * W:(w + 1) * W]), contact_count=(w == T // W - 1))
+        cc = cur.get("contact_count")
+        cur = cur["state_T"]
+        gpu_starts.append(cur.cpu().numpy().astype(np.float64)[idx])
+    sysm.sync_status()
+    orc_starts = [st[idx]]
+    for w in range(T // W):
+        orc_starts.append(orc.rollout(d, orc_starts[-1], a[w * W:(w + 1) * W, idx].astype(np.float64)))
+    ref, g = orc_starts[-1], gpu_starts[-1]
     err = np.abs(g[..., 0:3] - ref[..., 0:3]).max(axis=(1, 2))
-    assert np.median(err) <= 1e-3, np.sort(err)[-10:]
-    assert np.mean(err <= 1e-3) >= 0.9, np.sort(err)[-10:]
-    assert np.isfinite(got["state_T"].cpu().numpy()).all()
-    assert (got["contact_count"].cpu().numpy() > 0).mean() > 0.5  # the feet are on the ground
+    ok = branch_consistent_envs(d, gpu_starts[:-1], orc_starts[:-1], a[:, idx].astype(np.float64), W)
+    assert ok.mean() >= 0.9, (ok.sum(), len(idx))
+    assert err[ok].max() <= 1e-3, (np.sort(err[ok])[-5:], ok.sum(), len(idx))
+    assert np.isfinite(cur.cpu().numpy()).all()
+    assert (cc.cpu().numpy() > 0).mean() > 0.5  # the feet are on the ground
 
 
 def test_distribution_after_1000_steps(brax):

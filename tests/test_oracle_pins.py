@@ -746,3 +746,41 @@ def test_two_body_contact_velocity_changes(kind):
                 assert np.linalg.norm(J - jn * n) <= mu * jn + 1e-10
         if mu == 0.0:
             assert n_active >= 5
+
+
+# ----------------------------------------------------------------- environment layer (Sec. 4.2)
+def test_env_oracle_observation_reward_done_closed_forms():
+    """The environment layer's oracle (oracle/env.py) against closed forms: a
+    child spinning freely about the hinge axis of a frozen parent (no springs
+    acting, g = 0) turns by 2 atan(h w / 2) per substep, so its observed joint
+    angle advances by that much per step and its observed rate is w; the root
+    observation is the root's state; the reward of a frozen root is
+    healthy - ctrl_cost * sum clamp(a)^2, and done follows the root height."""
+    from oracle import env as oenv
+    w, h, subs = 0.7, 0.01, 1
+    d = hinge_system(gear=0.0, ca=0.0, I=0.8, ka=0.0, c=0.0, dt=h, substeps=subs)
+    d["stiffness"] = np.zeros_like(d["stiffness"])
+    st = state_of(d)
+    st[0, 1, 10:13] = [w, 0.0, 0.0]  # about the hinge axis (world x)
+    obs0 = oenv.observe(d, st)
+    assert obs0.shape == (1, oenv.obs_size(d)) and oenv.obs_size(d) == 13
+    spec = oenv.EnvSpec(forward_weight=2.0, healthy_reward=0.25, ctrl_cost=0.5, min_z=-1.0, max_z=1.0,
+                        auto_reset=False)
+    T = 6
+    acts = np.full((T, 1, 1), 1.7)  # clamped to 1 for the cost
+    sT, obs, rew, done = oenv.env_rollout(d, spec, st, st, acts)
+    step = 2 * math.atan(h * w / 2)
+    for t in range(T):
+        assert abs(obs[t, 0, 11] - (obs0[0, 11] + (t + 1) * step)) < 1e-12
+        assert abs(obs[t, 0, 12] - w) < 1e-12
+        assert np.array_equal(obs[t, 0, :11], np.concatenate([[st[0, 0, 2]], st[0, 0, 3:13]]))
+    assert np.allclose(rew, 0.25 - 0.5 * 1.0, atol=1e-15)  # frozen root: no progress
+    assert not done.any()
+    # done: a healthy range that excludes the root's height ends every step; the reset restores the state
+    spec2 = oenv.EnvSpec(forward_weight=2.0, healthy_reward=0.25, ctrl_cost=0.5, min_z=0.5, max_z=1.0,
+                         auto_reset=True)
+    reset = st.copy()
+    reset[0, 1, 10:13] = [-w, 0.0, 0.0]
+    sT2, obs2, rew2, done2 = oenv.env_rollout(d, spec2, st, reset, acts)
+    assert done2.all() and np.allclose(rew2, -0.5, atol=1e-15)
+    assert abs(obs2[0, 0, 12] - w) < 1e-12 and abs(obs2[1, 0, 12] + w) < 1e-12  # restarted from the reset state

@@ -66,3 +66,50 @@ def test_noalloc_refuses_rollouts_beyond_its_scratch(system):
     with pytest.raises(BraxError) as ei:
         system.rollout_backward_noalloc(st, a, ck, torch.zeros_like(st), K=K)
     assert ei.value.code == 7 and "scratch" in str(ei.value)
+
+
+def test_noalloc_chunked_schedule_allocates_nothing():
+    """With the chunked schedule forced on (chunks of two checkpoint
+    segments), the entry point takes the schedule's counter and flags from its
+    own array: two calls in a row on a fresh system match the static-schedule
+    reverse pass given a workspace, and the device's free memory does not
+    change across them (after a first call that sets the array up)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_13281_gb300.binding import _ptr, _stream, check
+    from paper_2106_13281_gb300.system import BraxSystem
+    d = S.quadruped()
+    chunked = BraxSystem(d)
+    chunked.set_schedule(2, 2)
+    static = BraxSystem(d)
+    static.set_schedule(0)
+    N, T, K = 200, 12, 4
+    runs = []
+    for seed in (61, 62):
+        st, a = inputs(d, N, T, seed)
+        ck = static.rollout(st, a, K=K, checkpoints=True)["checkpoints"]
+        rng = np.random.default_rng(seed)
+        gT = cuda(rng.normal(size=(N, static.B, 13)))
+        gtor = cuda(rng.normal(size=(T, N, 3)))
+        ref = static.rollout_backward(st, a, ck, gT, gtor, K=K)
+        runs.append((st, a, ck, gT, gtor, ref, torch.empty_like(a), torch.empty_like(st)))
+    L = chunked._L
+
+    def call(r):
+        st, a, ck, gT, gtor, _, ga, gs = r
+        check(L.brax_rollout_backward_noalloc(chunked.handle, N, T, K, _ptr(st), _ptr(a), _ptr(ck), _ptr(gT),
+                                              _ptr(gtor), _ptr(ga), _ptr(gs), _stream()))
+
+    call(runs[0])  # first call on the device: looks the array up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for r in runs:
+        call(r)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    chunked.sync_status()
+    assert free1 == free0, (free0, free1)
+    for st, a, ck, gT, gtor, (ref_a, ref_s), ga, gs in runs:
+        assert torch.isfinite(ga).all() and torch.isfinite(gs).all()
+        assert torch.allclose(ga, ref_a, rtol=1e-5, atol=1e-6)
+        assert torch.allclose(gs, ref_s, rtol=1e-5, atol=1e-6)
