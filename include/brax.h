@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define BRAX_DESC_VERSION 1
+#define BRAX_DESC_VERSION 2  /* 1: the descriptor without the variant fields at its end */
 
 /* Limits of one system (checked by brax_system_create). */
 #define BRAX_MAX_BODIES 32        /* one warp per body in a thread block */
@@ -125,6 +125,15 @@ typedef struct {
    * capsule-capsule, capsule-box (either order) */
   const int32_t* pair_a;        /* [P] collider index */
   const int32_t* pair_b;        /* [P] collider index */
+  /* version 2: variants (read only when version >= 2; zero / NULL = off) */
+  float linear_damping;         /* global: the potential integrator adds -linear_damping * v (1/s) */
+  float angular_damping_global; /* global: ... adds -angular_damping_global * w (1/s) */
+  int32_t gyroscopic;           /* 1: the potential integrator adds the gyroscopic torque
+                                   -w x (I_w w), I_w = R diag(inertia) R^T */
+  const int32_t* act_type;      /* [A] 0: torque actuator; 1: target-angle actuator (Sec. 3:
+                                   actions are "torques or target angles"): the action picks the
+                                   target (lo + hi)/2 + clamp(a, -1, 1) (hi - lo)/2 in the axis'
+                                   limit range and the torque is gear * (target - angle) */
 } brax_desc;
 
 typedef struct brax_system brax_system;

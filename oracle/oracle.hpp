@@ -125,6 +125,10 @@ struct System {
   // actuators
   std::vector<int> act_joint, act_axis;
   std::vector<double> gear;
+  std::vector<int> act_type;  // [A] 0: torque, 1: target angle
+  // variants of the potential integrator (0 / false: off)
+  double lin_damp = 0.0, ang_damp = 0.0;
+  bool gyro = false;
   // colliders
   std::vector<int> col_body, col_type;
   std::vector<double> col_pos, col_rot, radius, length, half, friction, elasticity;
@@ -331,14 +335,30 @@ template <class T> inline void joint_apply(const System& s, int j, const Body<T>
 // Sec. 3: actuators turn `actions` into torques.  READING: a torque actuator
 // applies gear * clamp(a, -1, 1) about the joint's world axis, on the child
 // and the opposite on the parent.
+// Torque actuator: tau = gear clamp(a, -1, 1) about the joint axis.
+// Target-angle actuator (Sec. 3: actions are "torques or target angles";
+// READING): the action picks a target angle in the axis' limit range,
+// theta* = (lo + hi)/2 + clamp(a, -1, 1) (hi - lo)/2, and the actuator is a
+// spring of stiffness gear toward it, tau = gear (theta* - theta), about the
+// same axis (the joint's angular damper damps it).
 template <class T> inline void actuator_apply(const System& s, int k, const T* act, const Frame<T>* fr,
                                               Wrench<T>* dp) {
   const int j = s.act_joint[k];
   const int p = s.parent[j], c = s.child[j];
-  V3<T> ax = mulc(fr[p].R, s.ap(j, s.act_axis[k]));
+  const int axis = s.act_axis[k];
+  V3<T> ax = mulc(fr[p].R, s.ap(j, axis));
   T a = vclamp(act[k], -1.0, 1.0);
   note_branch(40 + (val(act[k]) >= 1.0 ? 1 : (val(act[k]) <= -1.0 ? 2 : 0)));
-  V3<T> tau = (T(s.gear[k]) * a) * ax;
+  T mag = T(s.gear[k]) * a;
+  if (!s.act_type.empty() && s.act_type[k] == 1) {
+    T ang[3];
+    V3<T> P[3];
+    joint_angles(s, j, fr[p], fr[c], ang, P);
+    const double lo = s.lo[3 * j + axis], hi = s.hi[3 * j + axis];
+    T target = T(0.5 * (lo + hi)) + T(0.5 * (hi - lo)) * a;
+    mag = T(s.gear[k]) * (target - ang[axis]);
+  }
+  V3<T> tau = mag * ax;
   dp[c].tau = dp[c].tau + tau;
   dp[p].tau = dp[p].tau - tau;
 }
@@ -728,13 +748,27 @@ template <class T> void substep(const System& s, Body<T>* qp, const T* act, Diag
   std::vector<Accum<T>> acc(B);
   for (int b = 0; b < B; ++b) acc[b] = Accum<T>{mk(T(0.0), T(0.0), T(0.0)), mk(T(0.0), T(0.0), T(0.0)), 0};
   for (const auto& ct : contacts) respond(s, ct, qp, fr.data(), acc.data(), dg);
-  // potential integrator: v += h (F/m + g);  w += h I_w^-1 tau.  READING: no
-  // gyroscopic term, no global damping.
+  // potential integrator: v += h (F/m + g);  w += h I_w^-1 tau.  READING: by
+  // default no gyroscopic term and no global damping.  Variants (Sec. 6's
+  // conservation study and the usual engine options): global damping
+  // v += h (... - lin_damp v), w += h (... - ang_damp w); the gyroscopic
+  // torque -w x (I_w w), I_w = R diag(I) R^T, added to tau (Euler's equations
+  // of a free rigid body in the world frame).
   set_cat(FC_INTEGRATE);
   for (int b = 0; b < B; ++b) {
     V3<T> a = T(1.0 / s.mass[b]) * dp[b].F + cst<T>(s.g);
+    if (s.lin_damp != 0.0) a = a - T(s.lin_damp) * qp[b].v;
+    V3<T> tau = dp[b].tau;
+    if (s.gyro) {
+      const M3<T>& R = fr[b].R;
+      V3<T> wl = mulT(R, qp[b].w);
+      V3<T> Lw = mul(R, mk(T(s.inertia[3 * b]) * wl.x, T(s.inertia[3 * b + 1]) * wl.y, T(s.inertia[3 * b + 2]) * wl.z));
+      tau = tau - cross(qp[b].w, Lw);
+    }
+    V3<T> alpha = mul(fr[b].Ii, tau);
+    if (s.ang_damp != 0.0) alpha = alpha - T(s.ang_damp) * qp[b].w;
     qp[b].v = mask(s, &s.fpos[3 * b], qp[b].v + T(h) * a);
-    qp[b].w = mask(s, &s.frot[3 * b], qp[b].w + T(h) * mul(fr[b].Ii, dp[b].tau));
+    qp[b].w = mask(s, &s.frot[3 * b], qp[b].w + T(h) * alpha);
   }
   // collision integrator: mean contact update per body
   for (int b = 0; b < B; ++b) {

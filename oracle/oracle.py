@@ -64,6 +64,8 @@ class _Desc(C.Structure):
         ("col_rot", C.c_void_p), ("radius", C.c_void_p), ("length", C.c_void_p),
         ("half_extents", C.c_void_p), ("friction", C.c_void_p), ("elasticity", C.c_void_p),
         ("pair_a", C.c_void_p), ("pair_b", C.c_void_p),
+        ("linear_damping", C.c_double), ("angular_damping_global", C.c_double), ("gyroscopic", C.c_int32),
+        ("act_type", C.c_void_p),
     ]
 
 
@@ -94,6 +96,11 @@ class OracleSystem:
         d.baumgarte = float(desc["baumgarte"])
         d.contact_eps = float(desc["contact_eps"])
         d.average_contacts = int(desc.get("average_contacts", 1))
+        d.linear_damping = float(desc.get("linear_damping", 0.0))
+        d.angular_damping_global = float(desc.get("angular_damping_global", 0.0))
+        d.gyroscopic = int(desc.get("gyroscopic", 0))
+        if "act_type" in desc:
+            self._set(d, "act_type", np.ascontiguousarray(desc["act_type"], dtype=np.int32))
         for k in _F64:
             self._set(d, k, np.ascontiguousarray(desc[k], dtype=np.float64))
         for k in _I32:

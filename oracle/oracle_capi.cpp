@@ -32,6 +32,10 @@ typedef struct {
   const int32_t *col_body, *col_type;
   const double *col_pos, *col_rot, *radius, *length, *half_extents, *friction, *elasticity;
   const int32_t *pair_a, *pair_b;
+  // variants (zero / NULL: off)
+  double linear_damping, angular_damping_global;
+  int32_t gyroscopic;
+  const int32_t* act_type;
 } orc_desc;
 
 }  // extern "C"
@@ -53,6 +57,10 @@ System make_system(const orc_desc* d) {
   s.baumgarte = d->baumgarte;
   s.eps = d->contact_eps;
   s.average = d->average_contacts != 0;
+  s.lin_damp = d->linear_damping;
+  s.ang_damp = d->angular_damping_global;
+  s.gyro = d->gyroscopic != 0;
+  if (d->act_type) cp(s.act_type, d->act_type, d->n_actuators);
   cp(s.mass, d->mass, s.B);
   cp(s.inertia, d->inertia, 3 * s.B);
   cp(s.rest_pos, d->rest_pos, 3 * s.B);

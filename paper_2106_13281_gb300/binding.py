@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbrax_gb300.so")
 
-BRAX_DESC_VERSION = 1
+BRAX_DESC_VERSION = 2
 STATUS = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_DESCRIPTOR", 3: "CUDA", 4: "OUT_OF_MEMORY",
           5: "NONFINITE", 6: "TIMEOUT", 7: "WORKSPACE"}
 
@@ -65,6 +65,8 @@ class brax_desc(C.Structure):
         ("radius", C.c_void_p), ("length", C.c_void_p), ("half_extents", C.c_void_p),
         ("friction", C.c_void_p), ("elasticity", C.c_void_p),
         ("pair_a", C.c_void_p), ("pair_b", C.c_void_p),
+        ("linear_damping", C.c_float), ("angular_damping_global", C.c_float), ("gyroscopic", C.c_int32),
+        ("act_type", C.c_void_p),
     ]
 
 
@@ -156,11 +158,18 @@ def marshal_desc(desc: dict):
     d.baumgarte = float(desc["baumgarte"])
     d.contact_eps = float(desc["contact_eps"])
     d.average_contacts = int(desc.get("average_contacts", 1))
+    d.linear_damping = float(desc.get("linear_damping", 0.0))
+    d.angular_damping_global = float(desc.get("angular_damping_global", 0.0))
+    d.gyroscopic = int(desc.get("gyroscopic", 0))
     for keys, dt in ((_F32, np.float32), (_I32, np.int32), (_U8, np.uint8)):
         for k in keys:
             a = np.ascontiguousarray(np.asarray(desc[k]), dtype=dt)
             keep.append(a)
             setattr(d, k, a.ctypes.data if a.size else None)
+    if "act_type" in desc and len(desc["act_type"]):
+        a = np.ascontiguousarray(np.asarray(desc["act_type"]), dtype=np.int32)
+        keep.append(a)
+        d.act_type = a.ctypes.data
     return d, keep
 
 

@@ -283,7 +283,11 @@ __device__ __forceinline__ void joint_hinge_bwd(const JP& bp, const Pub& pp, con
   }
   float sc = L - bp.ca * dot(wr, P0);
   const bool has_act = bp.act[0] >= 0;
-  if (has_act) sc = fmaf(bp.gear[0], clamp1(act[0]), sc);
+  const bool angle_act = has_act && (bp.act_angle & 1);
+  if (has_act) {
+    if (angle_act) sc = fmaf(bp.gear[0], fmaf(bp.act_half[0], clamp1(act[0]), bp.act_mid[0]) - th, sc);
+    else sc = fmaf(bp.gear[0], clamp1(act[0]), sc);
+  }
   // ---- reverse
   // child gets F, tc = rc x F + tj; parent gets -F, tp = -(rp x F) - tj
   V3 gF = gFc - gFp;
@@ -302,10 +306,11 @@ __device__ __forceinline__ void joint_hinge_bwd(const JP& bp, const Pub& pp, con
   gP0 = fma3(-bp.ca * gsc, wr, gP0);
   if (has_act) {
     const float a = act[0];
-    if (a > -1.f && a < 1.f) gact[0] = fmaf(bp.gear[0], gsc, gact[0]);
+    if (a > -1.f && a < 1.f) gact[0] = fmaf(angle_act ? bp.gear[0] * bp.act_half[0] : bp.gear[0], gsc, gact[0]);
   }
-  // limit spring: d L / d th = -kl when active
-  const float gth = lim ? -bp.kl * gL : 0.f;
+  // limit spring: d L / d th = -kl when active; a target-angle actuator adds -gear
+  float gth = lim ? -bp.kl * gL : 0.f;
+  if (angle_act) gth = fmaf(-bp.gear[0], gsc, gth);
   const float r2 = fmaf(sy, sy, cx * cx);
   const float inv_r2 = r2 > 0.f ? __fdividef(1.f, r2) : 0.f;
   const float gsy = cx * inv_r2 * gth, gcx = -sy * inv_r2 * gth;
@@ -379,7 +384,12 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
       L[a] = bp.kl * (bp.hi[a] - th[a]);
       lim[a] = 1;
     }
-    if (bp.act[a] >= 0) L[a] = fmaf(bp.gear[a], clamp1(act[a]), L[a]);
+    if (bp.act[a] >= 0) {
+      if (bp.act_angle & (1 << a))
+        L[a] = fmaf(bp.gear[a], fmaf(bp.act_half[a], clamp1(act[a]), bp.act_mid[a]) - th[a], L[a]);
+      else
+        L[a] = fmaf(bp.gear[a], clamp1(act[a]), L[a]);
+    }
   }
   // ---- reverse
   V3 gF = gFc - gFp;
@@ -397,8 +407,10 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
     const float gL = dot(gtj, P[a]);
     gth[a] = lim[a] ? -bp.kl * gL : 0.f;
     if (bp.act[a] >= 0) {
+      const bool angle_act = (bp.act_angle & (1 << a)) != 0;
       const float av = act[a];
-      if (av > -1.f && av < 1.f) gact[a] = fmaf(bp.gear[a], gL, gact[a]);
+      if (av > -1.f && av < 1.f) gact[a] = fmaf(angle_act ? bp.gear[a] * bp.act_half[a] : bp.gear[a], gL, gact[a]);
+      if (angle_act) gth[a] = fmaf(-bp.gear[a], gL, gth[a]);
     }
   }
   float gm00 = 0.f, gm01 = 0.f, gm02 = 0.f, gm12 = 0.f, gm22 = 0.f;

@@ -190,7 +190,30 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   S6 gI;
   zero(gI);
   V3 gTt = zero3();
-  s6_mul_bwd(f.Ii, Tt, h * gw2, gI, gTt);
+  S6 gIw;  // adjoint of I_w = R diag(I) R^T (the gyroscopic term)
+  zero(gIw);
+  if (kGeneral && S.variants) {
+    // v1 = v + h (F/m + g - ld v);  w1 = w + h (Ii (T - w x I_w w) - ad w)
+    gvm = fma3(-h * S.lin_damp, gv2, gvm);
+    gwm = fma3(-h * S.ang_damp, gw2, gwm);
+    V3 Te = Tt;
+    V3 u = zero3();
+    S6 Iw;
+    if (S.gyro) {
+      Iw = inv_inertia_world(f.R, bp.I);
+      u = mul(Iw, s.w);
+      Te = Tt - cross(s.w, u);
+    }
+    s6_mul_bwd(f.Ii, Te, h * gw2, gI, gTt);
+    if (S.gyro) {  // c = w x u, u = I_w w, Te = T - c
+      const V3 gc = -gTt;
+      V3 gu = zero3();
+      cross_bwd(s.w, u, gc, gwm, gu);
+      s6_mul_bwd(Iw, s.w, gu, gIw, gwm);
+    }
+  } else {
+    s6_mul_bwd(f.Ii, Tt, h * gw2, gI, gTt);
+  }
   {
     float* o = bm.gwr + (b * 6) * 32 + lane;
     o[0] = gFt.x;
@@ -300,6 +323,7 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
   inv_inertia_bwd(f.R, bp.inv_I, gI, gR);
+  if (kGeneral && S.gyro) inv_inertia_bwd(f.R, bp.I, gIw, gR);
   float gq1[4] = {g.q[0], g.q[1], g.q[2], g.q[3]};
   qmat_bwd(s.qw, s.qx, s.qy, s.qz, gR, gq1);
   g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);

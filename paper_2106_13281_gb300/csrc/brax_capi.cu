@@ -65,7 +65,14 @@ struct Rejected {
 
 // Validate a descriptor and flatten it into the parameter blob.
 std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int* P_out) {
-  REQUIRE(d.version == BRAX_DESC_VERSION, "version: expected BRAX_DESC_VERSION");
+  REQUIRE(d.version == 1 || d.version == BRAX_DESC_VERSION, "version: expected 1 or BRAX_DESC_VERSION");
+  // a version-1 descriptor ends before the variant fields: they are off
+  const bool v2 = d.version >= 2;
+  const float lin_damp = v2 ? d.linear_damping : 0.f, ang_damp = v2 ? d.angular_damping_global : 0.f;
+  const int gyro = v2 ? (d.gyroscopic != 0) : 0;
+  const int32_t* act_type = v2 ? d.act_type : nullptr;
+  REQUIRE(std::isfinite(lin_damp) && lin_damp >= 0.f && std::isfinite(ang_damp) && ang_damp >= 0.f,
+          "linear_damping / angular_damping_global: must be finite and >= 0");
   const int B = d.n_bodies, J = d.n_joints, A = d.n_actuators, C = d.n_colliders, P = d.n_pairs;
   REQUIRE(B >= 1 && B <= BRAX_MAX_BODIES, "n_bodies: must be in [1, BRAX_MAX_BODIES]");
   REQUIRE(J >= 0 && J < B, "n_joints: must be in [0, n_bodies - 1]");
@@ -106,6 +113,7 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
     uint32_t fl = 0;
     for (int i = 0; i < 3; ++i) {
       bp.inv_I[i] = (float)(1.0 / d.inertia[3 * b + i]);
+      bp.I[i] = d.inertia[3 * b + i];
       if (d.frozen_pos[3 * b + i]) fl |= kFrozenPos0 << i;
       if (d.frozen_rot[3 * b + i]) fl |= kFrozenRot0 << i;
     }
@@ -210,6 +218,15 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
     REQUIRE(std::isfinite(d.gear[k]), "gear: not finite");
     bodies[c].act[ax] = k;
     bodies[c].gear[ax] = d.gear[k];
+    if (act_type) {
+      REQUIRE(act_type[k] == 0 || act_type[k] == 1, "act_type: must be 0 (torque) or 1 (target angle)");
+      if (act_type[k] == 1) {
+        const double lo = d.limit_lo[3 * j + ax] * deg, hi = d.limit_hi[3 * j + ax] * deg;
+        bodies[c].act_angle |= 1 << ax;
+        bodies[c].act_mid[ax] = (float)(0.5 * (lo + hi));
+        bodies[c].act_half[ax] = (float)(0.5 * (hi - lo));
+      }
+    }
   }
   // colliders, planes
   std::vector<int> plane_slot(C, -1);
@@ -337,6 +354,23 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
           for (int j = 0; j < 3; ++j) pr.bR[3 * i + j] = (float)R[i][j];
         }
       }
+      {  // broadphase bound (PairP::bound2)
+        auto seg_half = [&](int ci) {
+          double e0[3], e1[3];
+          capsule_local(ci, e0, e1);
+          const double dx = e1[0] - e0[0], dy = e1[1] - e0[1], dz = e1[2] - e0[2];
+          return 0.5 * std::sqrt(dx * dx + dy * dy + dz * dz);
+        };
+        double ra = seg_half(ca) + d.radius[ca], rb;
+        if (tb == BRAX_CAPSULE) {
+          rb = seg_half(cb) + d.radius[cb];
+        } else {
+          const float* he = d.half_extents + 3 * cb;
+          rb = std::sqrt((double)he[0] * he[0] + (double)he[1] * he[1] + (double)he[2] * he[2]);
+        }
+        const double bnd = (ra + rb) * (1.0 + 1e-4) + 1e-5;
+        pr.bound2 = (float)(bnd * bnd);
+      }
       const int idx = (int)pairs.size();
       pairs.push_back(pr);
       for (int side = 0; side < 2; ++side) {
@@ -395,6 +429,14 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   S.general = Pb > 0 ? 1 : 0;
   for (int j = 0; j < J; ++j)
     if (d.dof[j] == 3) S.general = 1;
+  // variants run in the general kernel (forward and reverse)
+  S.lin_damp = lin_damp;
+  S.ang_damp = ang_damp;
+  S.gyro = gyro;
+  S.variants = (lin_damp != 0.f || ang_damp != 0.f || gyro) ? 1 : 0;
+  for (int b = 0; b < B; ++b)
+    if (bodies[b].act_angle) S.variants = 1;
+  if (S.variants) S.general = 1;
   const double h = (double)d.dt / d.substeps;
   S.h = (float)h;
   S.beta_h = (float)(d.baumgarte / h);

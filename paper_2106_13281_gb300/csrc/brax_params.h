@@ -49,6 +49,12 @@ struct BodyP {
   float lo[3], hi[3];  // radians
   int32_t act[3];      // actuator index per joint axis, -1 none
   float gear[3];
+  // target-angle actuators (bit a: axis a's actuator drives the angle toward
+  // act_mid[a] + clamp(action) act_half[a], the middle and half width of the
+  // axis' limit range, with stiffness gear[a]); 0: all torque actuators
+  int32_t act_angle;
+  float act_mid[3], act_half[3];
+  float I[3];          // principal inertia (the gyroscopic term)
   int32_t n_children;
   int32_t children[BRAX_MAX_CHILDREN];
   int32_t n_points;
@@ -84,6 +90,14 @@ struct PairP {
   float a0[3], a1[3];
   float b0[3], b1[3];
   float bR[9];
+  // Broadphase: the two colliders' bounding spheres (centred at the capsule
+  // segment's midpoint, at the box centre) are disjoint, so the pair cannot
+  // touch, when the centres are more than sqrt(bound2) apart.  bound2 is the
+  // square of the summed radii (half segment + r; |half extents|) with a
+  // relative margin of 1e-4 and 1e-5 m, far above FP32 rounding.
+  float bound2;
+  // capsule a's segment midpoint offset from its start along its direction
+  // (0.5) is implicit; for a box the centre is b0.
 };
 
 struct PlaneP {
@@ -93,9 +107,10 @@ struct PlaneP {
 
 struct SysP {
   int32_t B, J, A, D, P, n_planes, substeps, average;
-  float h, beta_h, eps, pad0;  // beta_h = baumgarte / h
+  float h, beta_h, eps;  // beta_h = baumgarte / h
+  float lin_damp;        // global linear damping (1/s) of the potential integrator, 0: none
   float g[3];
-  float pad1;
+  float ang_damp;        // global angular damping (1/s), 0: none
   int32_t general;   // 1: the system has a 3-DOF joint or a body-body pair
   int32_t paired;    // 1: the blob carries SysP2/BodyP2 (two environments per thread)
   int32_t pair_off;  // byte offset of SysP2 in the blob
@@ -103,7 +118,8 @@ struct SysP {
   int32_t joint_order[BRAX_MAX_BODIES];  // child bodies in topological order (for default_qp)
   int32_t n_order;
   int32_t n_parents;  // bodies with at least one child
-  int32_t pad2[2];
+  int32_t gyro;       // 1: the potential integrator adds the gyroscopic torque -w x (I_w w)
+  int32_t variants;   // 1: damping, gyroscopic term or target-angle actuators (general kernel only)
 };
 
 // Two environments per thread (systems with hinge joints only and at most

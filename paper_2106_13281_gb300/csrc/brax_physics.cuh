@@ -229,6 +229,9 @@ struct HingeRegs {
   float lo[1], hi[1], gear[1];
   int act[1];
   int dof;
+  // systems with target-angle actuators run the general kernel (BodyP)
+  static constexpr int act_angle = 0;
+  float act_mid[1], act_half[1];
 };
 __device__ __forceinline__ HingeRegs hinge_regs(const BodyP& bp) {
   HingeRegs r;
@@ -299,7 +302,12 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
     if (th < bp.lo[0]) L = bp.kl * (bp.lo[0] - th);
     else if (th > bp.hi[0]) L = bp.kl * (bp.hi[0] - th);
     float sc = L - bp.ca * dot(wr, P0);
-    if (bp.act[0] >= 0) sc = fmaf(bp.gear[0], clamp1(act[0]), sc);
+    if (bp.act[0] >= 0) {
+      if (bp.act_angle & 1)  // target-angle actuator: a spring toward the picked angle
+        sc = fmaf(bp.gear[0], fmaf(bp.act_half[0], clamp1(act[0]), bp.act_mid[0]) - th, sc);
+      else
+        sc = fmaf(bp.gear[0], clamp1(act[0]), sc);
+    }
     tj = fma3(sc, P0, bp.ka * cross(Ac, P0));
   } else {
     const V3 P2 = mulc(pp.R, bp.ap + 6);
@@ -319,7 +327,12 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
       float L = 0.f;
       if (th[a] < bp.lo[a]) L = bp.kl * (bp.lo[a] - th[a]);
       else if (th[a] > bp.hi[a]) L = bp.kl * (bp.hi[a] - th[a]);
-      if (bp.act[a] >= 0) L = fmaf(bp.gear[a], clamp1(act[a]), L);
+      if (bp.act[a] >= 0) {
+        if (bp.act_angle & (1 << a))
+          L = fmaf(bp.gear[a], fmaf(bp.act_half[a], clamp1(act[a]), bp.act_mid[a]) - th[a], L);
+        else
+          L = fmaf(bp.gear[a], clamp1(act[a]), L);
+      }
       tj = fma3(L, Pk[a], tj);
     }
   }
@@ -550,6 +563,16 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
       const Pub Bq = read_pub(gm, pr.bb, lane);
       capsule_world(Bq.R, Bq.x, pr.b0, pr.b1, P2, d2);
     }
+    // broadphase (Sec. 7.2's future work): disjoint bounding spheres cannot
+    // touch; when no environment of the warp needs the narrow phase, skip it
+    // (an environment that does not need it would find no contact there)
+    const V3 dm = fma3(0.5f, d1, P1) - fma3(0.5f, d2, P2);
+    if (__all_sync(0xffffffffu, dot(dm, dm) > pr.bound2)) {
+      float4* sl = gm.slot4(k, 0) + lane;
+      sl[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      sl[32] = make_float4(0.f, 0.f, 0.f, 0.f);
+      return 0;
+    }
     float sp, tp;
     segment_closest(P1, d1, P2, d2, sp, tp);
     const V3 c1 = fma3(sp, d1, P1), c2 = fma3(tp, d2, P2);
@@ -572,6 +595,13 @@ __device__ __forceinline__ int pair_forward(const SysP& S, const BodyP* bodies, 
     } else {
       const Pub Bq = read_pub(gm, pr.bb, lane);
       box_world(Bq.R, Bq.x, pr.b0, pr.bR, Rb, cb);
+    }
+    const V3 dm = fma3(0.5f, d1, P1) - cb;  // broadphase, as for two capsules
+    if (__all_sync(0xffffffffu, dot(dm, dm) > pr.bound2)) {
+      float4* sl = gm.slot4(k, 0) + lane;
+      sl[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      sl[32] = make_float4(0.f, 0.f, 0.f, 0.f);
+      return 0;
     }
     const V3 Pl = mulT(Rb, P1 - cb);
     const V3 dl = mulT(Rb, d1);
@@ -739,8 +769,20 @@ __device__ __forceinline__ void integrate(const SysP& S, const BodyP& bp, GroupM
     }
   }
   const float h = S.h;
-  V3 v = fma3(h, fma3(bp.inv_mass, wr.F, ld3(S.g)), s.v);
-  V3 w = fma3(h, mul(f.Ii, wr.tau), s.w);
+  V3 v, w;
+  if (kGeneral && S.variants) {
+    // variants: global damping and the gyroscopic torque -w x (I_w w)
+    V3 a = fma3(bp.inv_mass, wr.F, ld3(S.g));
+    a = fma3(-S.lin_damp, s.v, a);
+    V3 tau = wr.tau;
+    if (S.gyro) tau = tau - cross(s.w, mul(inv_inertia_world(f.R, bp.I), s.w));
+    const V3 alpha = fma3(-S.ang_damp, s.w, mul(f.Ii, tau));
+    v = fma3(h, a, s.v);
+    w = fma3(h, alpha, s.w);
+  } else {
+    v = fma3(h, fma3(bp.inv_mass, wr.F, ld3(S.g)), s.v);
+    w = fma3(h, mul(f.Ii, wr.tau), s.w);
+  }
   if (bp.flags & kAnyFrozen) {
     v = mask3(bp.flags, v);
     w = mask3(bp.flags >> 3, w);

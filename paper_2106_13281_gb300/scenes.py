@@ -146,8 +146,12 @@ class SceneBuilder:
             angular_damping=angular_damping, limit_lo=lo, limit_hi=hi, limit_stiffness=limit_stiffness))
         return len(self.joints) - 1
 
-    def actuator(self, joint, axis=0, gear=1.0):
-        self.actuators.append(dict(joint=joint, axis=axis, gear=float(gear)))
+    def actuator(self, joint, axis=0, gear=1.0, kind="torque"):
+        """A torque actuator (torque = gear * clamp(a)), or with kind="angle" a
+        target-angle actuator (a spring of stiffness gear toward the angle the
+        action picks in the axis' limit range)."""
+        assert kind in ("torque", "angle")
+        self.actuators.append(dict(joint=joint, axis=axis, gear=float(gear), type=0 if kind == "torque" else 1))
         return len(self.actuators) - 1
 
     # colliders --------------------------------------------------------
@@ -206,6 +210,7 @@ class SceneBuilder:
             act_joint=np.array([a["joint"] for a in self.actuators], dtype=np.int32),
             act_axis=np.array([a["axis"] for a in self.actuators], dtype=np.int32),
             gear=np.array([a["gear"] for a in self.actuators], dtype=np.float64),
+            act_type=np.array([a["type"] for a in self.actuators], dtype=np.int32),
             col_body=np.array([c["body"] for c in self.colliders], dtype=np.int32),
             col_type=np.array([c["type"] for c in self.colliders], dtype=np.int32),
             col_pos=f(self.colliders, "pos", 3), col_rot=f(self.colliders, "rot", 4),
@@ -407,6 +412,43 @@ SCENES = dict(quadruped=quadruped, biped=biped, pendulum=pendulum, arm_box=arm_b
 
 
 # --------------------------------------------------------------------- seeded inputs
+def planar(desc, axis=1) -> dict:
+    """The planar masking of App. E (Halfcheetah): every body's position is
+    frozen along world axis `axis` and its rotation about the other two, so
+    motion stays in the plane normal to `axis` and turns only about it."""
+    d = dict(desc)
+    fp = np.array(desc["frozen_pos"], dtype=np.uint8).copy()
+    fr = np.array(desc["frozen_rot"], dtype=np.uint8).copy()
+    fp[:, axis] = 1
+    for k in range(3):
+        if k != axis:
+            fr[:, k] = 1
+    d["frozen_pos"], d["frozen_rot"] = fp, fr
+    return d
+
+
+def quadruped_variants() -> dict:
+    """The quadruped with the variants of the step switched on: target-angle
+    actuators at the knees (torque actuators at the hips), global linear and
+    angular damping, the gyroscopic torque, and an anisotropic torso inertia
+    (so that the gyroscopic term does not vanish)."""
+    d = quadruped()
+    d = dict(d)
+    n_act = len(d["act_joint"])
+    # joints alternate hip, knee per leg: knees are the children of thighs
+    knee = np.array([d["parent"][j] != 0 for j in d["act_joint"]], dtype=bool)
+    d["act_type"] = np.where(knee, 1, 0).astype(np.int32)
+    d["gear"] = np.where(knee, 200.0, np.asarray(d["gear"], dtype=np.float64))
+    d["linear_damping"] = 0.2
+    d["angular_damping_global"] = 0.5
+    d["gyroscopic"] = 1
+    inertia = np.array(d["inertia"], dtype=np.float64).copy()
+    inertia[0] = [0.8, 1.2, 1.6]
+    d["inertia"] = inertia
+    assert n_act == len(d["act_type"])
+    return d
+
+
 def joint_angle_centres(desc) -> np.ndarray:
     """Per-DOF centre of the initial angle distribution (radians): 0 where 0
     lies inside the limit range, else the midpoint of the range (the knees)."""
@@ -460,3 +502,5 @@ def capsule_on_box(inside=False) -> dict:
 
 SCENES["capsule_on_box"] = lambda joint=None: capsule_on_box(False)
 SCENES["capsule_in_box"] = lambda joint=None: capsule_on_box(True)
+SCENES["quadruped_variants"] = lambda joint=None: quadruped_variants()
+SCENES["quadruped_planar"] = lambda joint=None: planar(quadruped())

@@ -79,3 +79,33 @@ def test_linear_momentum_to_fp32_roundoff(brax, name):
     mass = float(np.sum(d["mass"]))
     vscale = np.abs(st[:, :, 7:10]).max() + 1.0
     assert np.abs(m1[:, :3] - m0[:, :3]).max() < 2e-4 * mass * vscale
+
+
+def test_energy_drift_falls_with_step_size_on_the_gpu(brax):
+    """The Sec. 6 conservation study as a sweep over the step size (Fig. 5:
+    non-conservation against h): the astronaut protocol (the biped; actuators,
+    damping, collisions and gravity off; random 1 m/s kicks) over 1 s at
+    h = 5, 2.5 and 1.25 ms on the GPU.  The energy drift falls as h falls,
+    as the oracle's does, and stays within twice the oracle's at every h."""
+    base = conservative(S.biped())
+    N = 64
+    rp, rr, ang = S.initial_conditions(base, N, 9, angle_sigma=0.05)
+    st = orc.default_qp(base, N, rp, rr, ang)
+    rng = np.random.default_rng(9)
+    kick = rng.normal(size=(N, st.shape[1], 3))
+    kick /= np.linalg.norm(kick, axis=-1, keepdims=True)
+    st[:, :, 7:10] = kick
+    st = st.astype(np.float32).astype(np.float64)
+    e0, _ = orc.energy_momentum(base, st)
+    drifts = []
+    for subs in (10, 20, 40):
+        d = dict(base, substeps=subs)
+        a = np.zeros((20, N, len(d["gear"])))
+        got = brax(d).rollout(cuda(st), cuda(a))["state_T"].cpu().numpy().astype(np.float64)
+        ref = orc.rollout(d, st, a)
+        e_gpu, _ = orc.energy_momentum(d, got)
+        e_ref, _ = orc.energy_momentum(d, ref)
+        dg, dr = np.mean(np.abs(e_gpu - e0) / e0), np.mean(np.abs(e_ref - e0) / e0)
+        assert dg <= 2.0 * dr + 1e-4, (subs, dg, dr)
+        drifts.append(dg)
+    assert drifts[2] < drifts[1] < drifts[0], drifts

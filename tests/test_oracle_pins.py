@@ -784,3 +784,81 @@ def test_env_oracle_observation_reward_done_closed_forms():
     sT2, obs2, rew2, done2 = oenv.env_rollout(d, spec2, st, reset, acts)
     assert done2.all() and np.allclose(rew2, -0.5, atol=1e-15)
     assert abs(obs2[0, 0, 12] - w) < 1e-12 and abs(obs2[1, 0, 12] + w) < 1e-12  # restarted from the reset state
+
+
+# ----------------------------------------------------------------- variants of the step
+def test_global_damping_closed_form():
+    """Global damping, no forces (g = 0): each substep scales v by
+    (1 - h d_l) and w by (1 - h d_a), and x follows the discrete sum
+    x_n = x0 + h v0 (1 - rho^n) / (1 - rho)."""
+    d = single_body(inertia=(0.2, 0.9, 1.7))
+    d["linear_damping"], d["angular_damping_global"] = 0.8, 1.3
+    v0, w0, x0 = np.array([1.0, -2.0, 0.5]), np.array([0.3, 0.1, -0.7]), np.array([0.1, 0.2, 0.3])
+    st = state_of(d, pos=x0, vel=v0, ang=w0)
+    T = 4
+    out = orc.rollout(d, st, np.zeros((T, 1, 0)))
+    n, h = T * 10, 0.005
+    rl, ra = 1 - h * 0.8, 1 - h * 1.3
+    assert np.allclose(out[0, 0, 7:10], v0 * rl ** n, atol=1e-13, rtol=0)
+    assert np.allclose(out[0, 0, 10:13], w0 * ra ** n, atol=1e-13, rtol=0)
+    assert np.allclose(out[0, 0, 0:3], x0 + h * v0 * (1 - rl ** n) / (1 - rl), atol=1e-13, rtol=0)
+
+
+def test_gyroscopic_term():
+    """The gyroscopic torque -w x (I_w w): (1) it vanishes for an isotropic
+    body; (2) one substep of a torque-free anisotropic body changes w by
+    -h I_w^-1 (w x I_w w) at the post-kinematic orientation (computed here);
+    (3) with it, a torque-free tumbling body keeps its angular momentum
+    I_w w to O(h), without it (w constant) the momentum swings."""
+    # (1)
+    d = single_body(inertia=(0.7, 0.7, 0.7))
+    st = state_of(d, quat=axis_angle([1, 2, 3], 0.9), ang=[1.0, -2.0, 3.0])
+    a = np.zeros((3, 1, 0))
+    on = orc.rollout(dict(d, gyroscopic=1), st, a)
+    assert np.abs(on - orc.rollout(d, st, a)).max() < 1e-13
+    # (2)
+    I = np.array([0.2, 0.9, 1.7])
+    d1 = single_body(inertia=tuple(I), dt=0.005, substeps=1)
+    w0 = np.array([1.0, -2.0, 3.0])
+    st = state_of(d1, quat=axis_angle([1, -1, 2], 0.7), ang=w0)
+    out = orc.rollout(dict(d1, gyroscopic=1), st, np.zeros((1, 1, 0)))
+    R = rotmats(out[0, 0, 3:7])
+    Iw = R @ np.diag(I) @ R.T
+    w1 = w0 - 0.005 * np.linalg.solve(Iw, np.cross(w0, Iw @ w0))
+    assert np.allclose(out[0, 0, 10:13], w1, atol=1e-13, rtol=0)
+    # (3)
+    d = single_body(inertia=tuple(I), dt=0.05, substeps=40)
+    st = state_of(d, quat=axis_angle([1, -1, 2], 0.7), ang=w0)
+
+    def momentum(s):
+        R = rotmats(s[0, 0, 3:7])
+        return R @ np.diag(I) @ R.T @ s[0, 0, 10:13]
+
+    L0 = momentum(st)
+    drift = {}
+    for g in (0, 1):
+        s = orc.rollout(dict(d, gyroscopic=g), st, np.zeros((20, 1, 0)))  # 1 s
+        drift[g] = np.linalg.norm(momentum(s) - L0) / np.linalg.norm(L0)
+    assert drift[1] < 0.02 and drift[0] > 10 * drift[1], drift
+
+
+def test_target_angle_actuator_converges_to_its_target():
+    """A hinge driven by a target-angle actuator (frozen parent, no gravity,
+    angular damping on): the action a picks theta* = (lo + hi)/2 + a (hi -
+    lo)/2 in the limit range, and the joint settles at theta* (where the
+    actuator's torque gear (theta* - theta) vanishes)."""
+    sb = S.SceneBuilder(dt=0.01, substeps=4, gravity=(0, 0, 0))
+    p = sb.body("P", 1.0, (1, 1, 1), (0, 0, 0), frozen_pos=(1, 1, 1), frozen_rot=(1, 1, 1))
+    cb = sb.body("C", 1.0, (0.5, 0.5, 0.5), (0, 0, 0))
+    j = sb.joint(p, cb, anchor=(0, 0, 0), axis=(1, 0, 0), ref=(0, 1, 0), stiffness=10000.0, spring_damping=5.0,
+                 angular_stiffness=40.0, angular_damping=2.0, limits=((-40, 60),), limit_stiffness=50.0)
+    sb.actuator(j, 0, 20.0, kind="angle")
+    d = sb.build()
+    assert list(d["act_type"]) == [1]
+    st = state_of(d)
+    for a in (-0.6, 0.25, 1.7):
+        out = orc.rollout(d, st, np.full((1500, 1, 1), a))  # 15 s, about 30 decay times
+        lo, hi = math.radians(-40), math.radians(60)
+        target = 0.5 * (lo + hi) + 0.5 * (hi - lo) * min(max(a, -1), 1)
+        assert abs(orc.joint_angles(d, out)[0, 0] - target) < 1e-6, a
+        assert np.abs(out[0, 1, 10:13]).max() < 1e-6
