@@ -114,3 +114,33 @@ def test_schedule_plan_host_logic(lib):
         n, s = plan(lib, 1, 0, units, T, slots)
         if n:
             assert s >= 16 and (n - 1) * s < T <= n * s
+
+
+def test_variant_fields_validated(lib):
+    """Descriptor version 2 (the variants): invalid actuator kinds and
+    negative damping are rejected before any CUDA call; an unknown version is
+    rejected; a version-1 descriptor is read without the variant fields, so
+    their (invalid) contents are never looked at."""
+    d = S.quadruped()
+    d["act_type"] = np.full(len(d["act_joint"]), 2, dtype=np.int32)
+    rc, h, msg = create(lib, d)
+    assert rc == 2 and "act_type" in msg
+    d = S.quadruped()
+    d["linear_damping"] = -1.0
+    rc, h, msg = create(lib, d)
+    assert rc == 2 and "damping" in msg
+    for version, ok in ((3, False), (1, True)):
+        dd = S.quadruped()
+        dd["act_type"] = np.full(len(dd["act_joint"]), 7, dtype=np.int32)
+        dd["angular_damping_global"] = -5.0
+        desc, keep = bnd.marshal_desc(dd)
+        desc.version = version
+        hh = C.c_void_p()
+        rc = lib.brax_system_create(C.byref(desc), C.byref(hh))
+        msg = lib.brax_last_error().decode()
+        if ok:  # validation passed (a GPU-less machine then fails at the first CUDA call)
+            assert rc != 2, msg
+            if rc == 0:
+                lib.brax_system_destroy(hh)
+        else:
+            assert rc == 2 and "version" in msg

@@ -85,8 +85,11 @@ def test_energy_drift_falls_with_step_size_on_the_gpu(brax):
     """The Sec. 6 conservation study as a sweep over the step size (Fig. 5:
     non-conservation against h): the astronaut protocol (the biped; actuators,
     damping, collisions and gravity off; random 1 m/s kicks) over 1 s at
-    h = 5, 2.5 and 1.25 ms on the GPU.  The energy drift falls as h falls,
-    as the oracle's does, and stays within twice the oracle's at every h."""
+    h = 5, 2.5 and 1.25 ms on the GPU.  The median energy drift over the
+    environments falls as h falls, as the oracle's does, and stays within
+    twice the oracle's at every h (the median: one of these 64 kicked
+    configurations is unstable under the explicit springs in the oracle
+    itself, at every h)."""
     base = conservative(S.biped())
     N = 64
     rp, rr, ang = S.initial_conditions(base, N, 9, angle_sigma=0.05)
@@ -105,7 +108,7 @@ def test_energy_drift_falls_with_step_size_on_the_gpu(brax):
         ref = orc.rollout(d, st, a)
         e_gpu, _ = orc.energy_momentum(d, got)
         e_ref, _ = orc.energy_momentum(d, ref)
-        dg, dr = np.mean(np.abs(e_gpu - e0) / e0), np.mean(np.abs(e_ref - e0) / e0)
+        dg, dr = np.median(np.abs(e_gpu - e0) / e0), np.median(np.abs(e_ref - e0) / e0)
         assert dg <= 2.0 * dr + 1e-4, (subs, dg, dr)
         drifts.append(dg)
     assert drifts[2] < drifts[1] < drifts[0], drifts
