@@ -276,7 +276,7 @@ def run_ours(args):
     h_out = torch.empty_like(h_state0).pin_memory()
 
     # the actions stream in on a copy stream in chunks (16 steps, doubling up
-    # to 250) while the previous chunk runs (BraxSystem.rollout_streamed)
+    # to 250) while the previous chunk runs (brax_rollout_streamed)
     e2e_bufs = {}
     e2e_chunk, e2e_first = 250, args.e2e_first_steps
 
@@ -363,8 +363,9 @@ def run_ours(args):
         "data": "synthetic (seeded PCG64 actions uniform[-1,1], initial joint angles N(0,0.1^2), heights 0.75+U(0,0.05))",
         "config": headline_config(N, T, int(d["substeps"]), float(d["dt"]), d["gear"].shape[0], world),
         "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "BraxSystem.rollout_streamed (pinned host inputs, chunks of %d steps doubling to %d, "
-                       "overlapped with compute)" % (min(e2e_first, e2e_chunk), e2e_chunk),
+                "api": "brax_rollout_streamed (C ABI; pinned host state and actions in, state out; chunks of %d "
+                       "steps doubling to %d on the system's copy stream, overlapped with compute)"
+                       % (min(e2e_first, e2e_chunk), e2e_chunk),
                 "gpu_launches_per_step": e2e_launches},
         "gpu_launches": args.steps,
         "fwd_bwd": {"value": fwd_bwd_value, "unit": "env-steps/s", "steps": fb_steps, "checkpoint_every": K,

@@ -242,6 +242,27 @@ int brax_env_rollout(const brax_system* sys, const brax_env_params* env, int64_t
                      const float* state0, const float* reset_state, const float* actions, float* state_T, float* obs,
                      float* reward, uint8_t* done, void* stream);
 
+/* ------------------------------------------------------------ rollouts from host memory
+ * brax_rollout with its inputs and output in host memory: state0 [N,B,13]
+ * and actions [T,N,A] are copied to the device and state_T [N,B,13] back,
+ * all within the call's stream order.  The actions travel in chunks (the
+ * first of first_steps steps, each next one twice as long, up to
+ * chunk_steps) on a copy stream the system owns, double-buffered, while the
+ * previous chunk is stepped on `stream`; each chunk is one brax_rollout
+ * launch continuing from the previous chunk's state, so the result equals
+ * one launch over all T steps (bitwise).  Host arrays must be pinned
+ * (cudaHostAlloc / cudaHostRegister) for the copies to overlap the compute.
+ * workspace: device scratch of at least brax_streamed_workspace_size bytes
+ * (two action chunks and two states), 256-byte aligned.  The call returns
+ * once the work is enqueued; state_T is valid after `stream` synchronises.
+ * Calls on one system must not overlap (they share its copy stream and
+ * events).  Errors: INVALID_ARGUMENT, WORKSPACE, CUDA.  The first call on a
+ * system creates its copy stream and events (no device memory). */
+int brax_streamed_workspace_size(const brax_system* sys, int64_t n_envs, int32_t chunk_steps, size_t* bytes);
+int brax_rollout_streamed(const brax_system* sys, int64_t n_envs, int32_t T, const float* h_state0,
+                          const float* h_actions, float* h_state_T, int32_t chunk_steps, int32_t first_steps,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
 /* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K). */
 int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, size_t* bytes);
 

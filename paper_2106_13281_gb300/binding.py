@@ -24,7 +24,8 @@ EXPORTS = ["brax_system_create", "brax_system_destroy", "brax_system_info", "bra
            "brax_rollout", "brax_workspace_size", "brax_rollout_backward", "brax_batch_create",
            "brax_batch_destroy", "brax_batch_offsets", "brax_batch_rollout", "brax_batch_workspace_size",
            "brax_batch_rollout_backward", "brax_sync_status", "brax_last_error", "brax_rollout_backward_noalloc",
-           "brax_autotune", "brax_batch_autotune", "brax_env_obs_size", "brax_env_rollout"]
+           "brax_autotune", "brax_batch_autotune", "brax_env_obs_size", "brax_env_rollout",
+           "brax_streamed_workspace_size", "brax_rollout_streamed"]
 
 BRAX_TUNE_FORWARD, BRAX_TUNE_REVERSE = 1, 2
 
@@ -113,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         L.brax_batch_autotune.argtypes = [P, i32, i32, P, P, i32, P, C.POINTER(i32), C.POINTER(C.c_float)]
         L.brax_rollout_backward_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P]
         L.brax_env_obs_size.argtypes = [P, C.POINTER(i32)]
+        L.brax_streamed_workspace_size.argtypes = [P, i64, i32, C.POINTER(C.c_size_t)]
+        L.brax_rollout_streamed.argtypes = [P, i64, i32, P, P, P, i32, i32, P, C.c_size_t, P]
         L.brax_env_rollout.argtypes = [P, C.POINTER(brax_env_params), i64, i32, P, P, P, P, P, P, P, P]
         if hasattr(L, "brax_system_set_launch"):
             L.brax_system_set_launch.argtypes = [P, i32, i32]

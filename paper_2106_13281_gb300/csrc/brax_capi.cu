@@ -782,6 +782,14 @@ void brax_system_destroy(brax_system* s) {
   cudaFree(s->d_blob);
   cudaFree(s->d_status);
   sched_free(s->sched);
+  if (s->copy_stream) {
+    cudaStreamDestroy(s->copy_stream);
+    cudaEventDestroy(s->ev_start);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(s->ev_ready[i]);
+      cudaEventDestroy(s->ev_free[i]);
+    }
+  }
   delete s;
 }
 
@@ -981,6 +989,90 @@ int brax_rollout(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
                  void* stream) {
   return rollout_impl(s, n_envs, T, K, state0, actions, state_T, checkpoints, torso_traj, contact_count, stream,
                       nullptr);
+}
+
+int brax_streamed_workspace_size(const brax_system* s, int64_t n_envs, int32_t chunk_steps, size_t* bytes) {
+  if (!s || !bytes || n_envs < 0 || chunk_steps < 1)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_streamed_workspace_size: bad arguments");
+  const size_t act = ((size_t)chunk_steps * n_envs * s->A * sizeof(float) + 255) & ~(size_t)255;
+  const size_t st = ((size_t)n_envs * s->B * 13 * sizeof(float) + 255) & ~(size_t)255;
+  *bytes = 2 * act + 2 * st;
+  return BRAX_OK;
+}
+
+int brax_rollout_streamed(const brax_system* s, int64_t n_envs, int32_t T, const float* h_state0,
+                          const float* h_actions, float* h_state_T, int32_t chunk_steps, int32_t first_steps,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  if (!s || n_envs < 0 || T < 0 || chunk_steps < 1 || first_steps < 1)
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_streamed: bad arguments");
+  if (n_envs == 0) return BRAX_OK;
+  if (!h_state0 || !h_state_T || (T > 0 && s->A > 0 && !h_actions))
+    return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_streamed: null host array");
+  const int32_t C = std::max(1, std::min(chunk_steps, std::max(T, 1)));
+  size_t need = 0;
+  brax_streamed_workspace_size(s, n_envs, C, &need);
+  if (!workspace || workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(BRAX_ERR_WORKSPACE, "brax_rollout_streamed: workspace missing, too small or not 256-byte aligned");
+  brax_system* ms = const_cast<brax_system*>(s);
+  std::lock_guard<std::mutex> lk(ms->stream_mu);
+  cudaError_t e = cudaSuccess;
+  if (!ms->copy_stream) {
+    e = cudaStreamCreateWithFlags(&ms->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ms->ev_start, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&ms->ev_ready[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ms->ev_free[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "brax_rollout_streamed: stream/event creation");
+  }
+  const cudaStream_t st = as_stream(stream), cs = ms->copy_stream;
+  const size_t act_bytes = ((size_t)C * n_envs * s->A * sizeof(float) + 255) & ~(size_t)255;
+  const size_t state_bytes = (size_t)n_envs * s->B * 13 * sizeof(float);
+  const size_t state_pad = (state_bytes + 255) & ~(size_t)255;
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  float* act_buf[2] = {reinterpret_cast<float*>(base), reinterpret_cast<float*>(base + act_bytes)};
+  float* st_buf[2] = {reinterpret_cast<float*>(base + 2 * act_bytes),
+                      reinterpret_cast<float*>(base + 2 * act_bytes + state_pad)};
+  // chunks: first_steps, doubling up to C
+  std::vector<std::pair<int32_t, int32_t>> chunks;
+  for (int32_t t0 = 0, n = std::min(first_steps, C); t0 < T; t0 += n, n = std::min(C, 2 * n))
+    chunks.push_back({t0, std::min(T, t0 + n)});
+  const size_t row = (size_t)n_envs * s->A * sizeof(float);
+  // the copy stream starts after the workspace's previous users on `stream`
+  e = cudaEventRecord(ms->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ms->ev_start, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st_buf[0], h_state0, state_bytes, cudaMemcpyHostToDevice, cs);
+  auto upload = [&](size_t i) -> cudaError_t {
+    const int b = (int)(i % 2);
+    cudaError_t r = cudaSuccess;
+    if (i >= 2) r = cudaStreamWaitEvent(cs, ms->ev_free[b], 0);  // the buffer's previous chunk is done
+    const size_t nb = (size_t)(chunks[i].second - chunks[i].first) * row;
+    if (r == cudaSuccess && nb)
+      r = cudaMemcpyAsync(act_buf[b], h_actions + (size_t)chunks[i].first * n_envs * s->A, nb,
+                          cudaMemcpyHostToDevice, cs);
+    if (r == cudaSuccess) r = cudaEventRecord(ms->ev_ready[b], cs);
+    return r;
+  };
+  if (chunks.empty()) {  // T == 0: the state goes back unchanged
+    if (e == cudaSuccess) e = cudaEventRecord(ms->ev_ready[0], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ms->ev_ready[0], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_state_T, st_buf[0], state_bytes, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_streamed");
+  }
+  if (e == cudaSuccess) e = upload(0);
+  int cur = 0;
+  for (size_t i = 0; i < chunks.size() && e == cudaSuccess; ++i) {
+    if (i + 1 < chunks.size()) e = upload(i + 1);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ms->ev_ready[i % 2], 0);
+    if (e != cudaSuccess) break;
+    const int rc = brax_rollout(s, n_envs, chunks[i].second - chunks[i].first, 1, st_buf[cur], act_buf[i % 2],
+                                st_buf[1 - cur], nullptr, nullptr, nullptr, stream);
+    if (rc != BRAX_OK) return rc;
+    e = cudaEventRecord(ms->ev_free[i % 2], st);
+    cur = 1 - cur;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_state_T, st_buf[cur], state_bytes, cudaMemcpyDeviceToHost, st);
+  return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_streamed");
 }
 
 int brax_env_obs_size(const brax_system* s, int32_t* obs_dim) {

@@ -1,6 +1,7 @@
 // Host-side definition of a system handle (shared by the C ABI translation
 // units).
 #pragma once
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -48,6 +49,10 @@ struct brax_system {
   int sched_first = 0;              // first item handed out (the wait test starts past chunk 0)
   int64_t sched_wait_ns = 2000000000;
   mutable brax::SchedScratch sched;
+  // brax_rollout_streamed's copy stream and events (created on first use).
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  std::mutex stream_mu;
   // The last brax_rollout launch: blocks launched, chunks (0 = static) and
   // steps per chunk (reported by brax_system_last_rollout).
   mutable int64_t last_grid = 0;

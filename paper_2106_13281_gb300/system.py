@@ -214,56 +214,32 @@ class BraxSystem:
 
     def rollout_streamed(self, h_state0, h_actions, h_state_T, chunk_steps: int = 100, bufs: dict | None = None,
                          first_steps: int = 16):
-        """Rollout whose inputs live in pinned host memory: the actions stream
-        to the device in chunks on a copy stream while the previous chunk is
-        being stepped (double-buffered), and the final state is copied back
-        into the pinned h_state_T.  Chunks start at `first_steps` steps and
-        double up to `chunk_steps`, so that the copy nothing overlaps (the
-        state and the first chunk) is short.  A chunk is one brax_rollout
-        launch continuing from the previous chunk's state, so the result
-        equals one launch over all steps.  `bufs` (a dict, filled on first
-        use) keeps the device buffers between calls.  Returns the number of
-        kernel launches."""
+        """Rollout whose inputs and output live in pinned host memory
+        (brax_rollout_streamed): the actions stream to the device in chunks on
+        the system's copy stream while the previous chunk is being stepped,
+        and the final state is copied back into the pinned h_state_T.  Chunks
+        start at `first_steps` steps and double up to `chunk_steps`; the
+        result equals one launch over all steps.  `bufs` (a dict, filled on
+        first use) keeps the device workspace between calls.  Returns the
+        number of rollout launches."""
         N, T = h_state0.shape[0], h_actions.shape[0]
         if not (h_state0.is_pinned() and h_actions.is_pinned() and h_state_T.is_pinned()):
             raise ValueError("rollout_streamed: host tensors must be pinned")
+        for t, shape, name in ((h_state0, (N, self.B, 13), "h_state0"), (h_actions, (T, N, self.A), "h_actions"),
+                               (h_state_T, (N, self.B, 13), "h_state_T")):
+            if t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"{name}: expected a contiguous float32 tensor of shape {shape}")
         bufs = {} if bufs is None else bufs
-        C = max(1, min(int(chunk_steps), T))
-        key = (N, C, self.A)
-        if bufs.get("key") != key:
-            bufs.clear()
-            bufs["key"] = key
-            bufs["act"] = [torch.empty((C, N, self.A), device="cuda") for _ in range(2)]
-            bufs["st"] = [torch.empty((N, self.B, 13), device="cuda") for _ in range(2)]
-            bufs["copy"] = torch.cuda.Stream()
-        act, st, cs = bufs["act"], bufs["st"], bufs["copy"]
-        comp = torch.cuda.current_stream()
-        ready = [torch.cuda.Event() for _ in range(2)]
-        free = [torch.cuda.Event() for _ in range(2)]
-        with torch.cuda.stream(cs):
-            cs.wait_stream(comp)  # the buffers' previous users are done
-            st[0].copy_(h_state0, non_blocking=True)
-        chunks = stream_chunks(T, C, first_steps)
-
-        def upload(i):
-            t0, t1 = chunks[i]
-            with torch.cuda.stream(cs):
-                if i >= 2:
-                    cs.wait_event(free[i % 2])
-                act[i % 2][: t1 - t0].copy_(h_actions[t0:t1], non_blocking=True)
-                ready[i % 2].record(cs)
-
-        upload(0)
-        cur = 0
-        for i, (t0, t1) in enumerate(chunks):
-            if i + 1 < len(chunks):
-                upload(i + 1)
-            comp.wait_event(ready[i % 2])
-            self.rollout(st[cur], act[i % 2][: t1 - t0], state_T=st[1 - cur])
-            free[i % 2].record(comp)
-            cur = 1 - cur
-        h_state_T.copy_(st[cur], non_blocking=True)
-        return len(chunks)
+        Cn = max(1, min(int(chunk_steps), max(T, 1)))
+        nbytes = C.c_size_t()
+        check(self._L.brax_streamed_workspace_size(self._h, N, Cn, C.byref(nbytes)))
+        ws = bufs.get("ws")
+        if ws is None or ws.numel() < nbytes.value:
+            ws = bufs["ws"] = torch.empty((max(nbytes.value, 1),), device="cuda", dtype=torch.uint8)
+        check(self._L.brax_rollout_streamed(self._h, N, T, h_state0.data_ptr(), h_actions.data_ptr(),
+                                            h_state_T.data_ptr(), Cn, int(first_steps), _ptr(ws), ws.numel(),
+                                            _stream()))
+        return len(stream_chunks(T, Cn, first_steps)) if T > 0 else 0
 
     # ---------------------------------------------------------------- backward
     def workspace_size(self, n_envs, T, K):
