@@ -94,7 +94,8 @@ typedef struct {
   /* joints [J]: springs between a parent and a child body (Sec. 3, 7.1) */
   const int32_t* parent;        /* [J] body index */
   const int32_t* child;         /* [J] body index; a body is the child of at most one joint */
-  const int32_t* dof;           /* [J] 1 (hinge) or 3 */
+  const int32_t* dof;           /* [J] 1 (hinge), 2 (universal: the twist about the joint frame's z
+                                   axis is held by a spring of angular_stiffness) or 3 */
   const float* parent_offset;   /* [J][3] anchor in the parent frame */
   const float* child_offset;    /* [J][3] anchor in the child frame */
   const float* parent_frame;    /* [J][4] joint frame in the parent (x = hinge axis) */

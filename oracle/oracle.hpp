@@ -325,6 +325,14 @@ template <class T> inline void joint_apply(const System& s, int j, const Body<T>
     tc = tc + tl;
     tp = tp - tl;
   }
+  if (s.dof[j] == 2) {
+    // 2-DOF (universal) joint, READING: the twist about the third joint axis
+    // is held at 0 by a spring of the alignment stiffness ka, as the hinge's
+    // off-axis rotations are
+    V3<T> tw = (T(-s.ka[j]) * ang[2]) * P[2];
+    tc = tc + tw;
+    tp = tp - tw;
+  }
   dp[c].F = dp[c].F + F;
   dp[c].tau = dp[c].tau + tc;
   dp[p].F = dp[p].F - F;
@@ -866,6 +874,7 @@ inline double energy(const System& s, const Body<double>* qp) {
       V3<double> Ac = mulc(fr[c].R, s.ac(j, 0));
       E += s.ka[j] * (1.0 - dot(Ac, P[0]));
     }
+    if (s.dof[j] == 2) E += 0.5 * s.ka[j] * ang[2] * ang[2];
     for (int a = 0; a < s.dof[j]; ++a) {
       double lo = s.lo[3 * j + a], hi = s.hi[3 * j + a], ex = 0.0;
       if (ang[a] < lo) ex = lo - ang[a];

@@ -384,6 +384,7 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
       L[a] = bp.kl * (bp.hi[a] - th[a]);
       lim[a] = 1;
     }
+    if (a == 2 && bp.dof == 2) L[a] = -bp.ka * th[2];  // the 2-DOF joint's twist spring
     if (bp.act[a] >= 0) {
       if (bp.act_angle & (1 << a))
         L[a] = fmaf(bp.gear[a], fmaf(bp.act_half[a], clamp1(act[a]), bp.act_mid[a]) - th[a], L[a]);
@@ -406,6 +407,7 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
     gC[a] = zero3();
     const float gL = dot(gtj, P[a]);
     gth[a] = lim[a] ? -bp.kl * gL : 0.f;
+    if (a == 2 && bp.dof == 2) gth[a] = -bp.ka * gL;
     if (bp.act[a] >= 0) {
       const bool angle_act = (bp.act_angle & (1 << a)) != 0;
       const float av = act[a];

@@ -137,7 +137,7 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   for (int j = 0; j < J; ++j) {
     const int p = d.parent[j], c = d.child[j];
     REQUIRE(p >= 0 && p < B && c >= 0 && c < B && p != c, "joint parent/child: out of range or equal");
-    REQUIRE(d.dof[j] == 1 || d.dof[j] == 3, "dof: must be 1 or 3");
+    REQUIRE(d.dof[j] >= 1 && d.dof[j] <= 3, "dof: must be 1, 2 or 3");
     BodyP& bc = bodies[c];
     REQUIRE(bc.joint < 0, "child: a body may be the child of only one joint");
     REQUIRE(bodies[p].n_children < BRAX_MAX_CHILDREN, "parent: more than BRAX_MAX_CHILDREN children");
@@ -188,6 +188,10 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
       REQUIRE(std::isfinite(d.limit_lo[3 * j + a]) && std::isfinite(d.limit_hi[3 * j + a]), "limits: not finite");
       bc.lo[a] = (float)(d.limit_lo[3 * j + a] * deg);
       bc.hi[a] = (float)(d.limit_hi[3 * j + a] * deg);
+    }
+    if (d.dof[j] == 2) {  // the third axis has no limit: its twist spring holds it (joint_forward)
+      bc.lo[2] = -3.14159265358979323846f;
+      bc.hi[2] = 3.14159265358979323846f;
     }
   }
   // topological order of joints (children of placed bodies)
@@ -428,7 +432,7 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   S.average = d.average_contacts ? 1 : 0;
   S.general = Pb > 0 ? 1 : 0;
   for (int j = 0; j < J; ++j)
-    if (d.dof[j] == 3) S.general = 1;
+    if (d.dof[j] >= 2) S.general = 1;
   // variants run in the general kernel (forward and reverse)
   S.lin_damp = lin_damp;
   S.ang_damp = ang_damp;

@@ -327,6 +327,9 @@ __device__ __forceinline__ Wrench joint_forward(const JP& bp, const Pub& pp, con
       float L = 0.f;
       if (th[a] < bp.lo[a]) L = bp.kl * (bp.lo[a] - th[a]);
       else if (th[a] > bp.hi[a]) L = bp.kl * (bp.hi[a] - th[a]);
+      // 2-DOF (universal) joint: the twist about the third axis is held at 0
+      // by a spring of the alignment stiffness (its limits never fire)
+      if (a == 2 && bp.dof == 2) L = -bp.ka * th[2];
       if (bp.act[a] >= 0) {
         if (bp.act_angle & (1 << a))
           L = fmaf(bp.gear[a], fmaf(bp.act_half[a], clamp1(act[a]), bp.act_mid[a]) - th[a], L);

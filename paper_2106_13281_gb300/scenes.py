@@ -449,6 +449,36 @@ def quadruped_variants() -> dict:
     return d
 
 
+def quadruped_2dof() -> dict:
+    """The quadruped with 2-DOF (universal) hips: axis 0 swings the leg about
+    the vertical (+-30 deg), axis 1 lifts it about the horizontal axis across
+    the leg (+-20 deg); the twist about the leg is held by the joint's
+    alignment spring.  12 torque actuators (gear 150)."""
+    sb = SceneBuilder(dt=0.05, substeps=10, gravity=(0, 0, -9.81))
+    jc = dict(QUADRUPED_JOINT)
+    torso_z = 0.75
+    t = sb.body("torso", 10.0, UNIT_INERTIA, (0, 0, torso_z))
+    sb.collider(t, CAPSULE, radius=0.25, length=0.5, friction=1.0)
+    ground = sb.plane(friction=1.0)
+    sb.pair(sb.collider_of(t), ground)
+    ez = np.array([0.0, 0, 1])
+    for k in range(4):
+        phi = np.deg2rad(45 + 90 * k)
+        d = np.array([np.cos(phi), np.sin(phi), 0.0])
+        hip = np.array([0, 0, torso_z]) + 0.25 * d
+        knee = hip + 0.4 * d
+        th = sb.capsule_body(f"thigh{k}", 1.0, 0.08, 0.4, hip + 0.2 * d, d, inertia=UNIT_INERTIA)
+        sh = sb.capsule_body(f"shin{k}", 1.0, 0.08, 0.4, knee + 0.2 * d, d, inertia=UNIT_INERTIA)
+        jh = sb.joint(t, th, hip, axis=ez, ref=np.cross(ez, d), dof=2, limits=((-30, 30), (-20, 20)), **jc)
+        jk = sb.joint(th, sh, knee, axis=np.cross(ez, d), ref=d, limits=((30, 70),), **jc)
+        sb.actuator(jh, 0, 150.0)
+        sb.actuator(jh, 1, 150.0)
+        sb.actuator(jk, 0, 150.0)
+        sb.pair(sb.collider_of(th), ground)
+        sb.pair(sb.collider_of(sh), ground)
+    return sb.build()
+
+
 def joint_angle_centres(desc) -> np.ndarray:
     """Per-DOF centre of the initial angle distribution (radians): 0 where 0
     lies inside the limit range, else the midpoint of the range (the knees)."""
@@ -504,3 +534,4 @@ SCENES["capsule_on_box"] = lambda joint=None: capsule_on_box(False)
 SCENES["capsule_in_box"] = lambda joint=None: capsule_on_box(True)
 SCENES["quadruped_variants"] = lambda joint=None: quadruped_variants()
 SCENES["quadruped_planar"] = lambda joint=None: planar(quadruped())
+SCENES["quadruped_2dof"] = lambda joint=None: quadruped_2dof()

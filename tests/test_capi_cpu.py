@@ -44,7 +44,7 @@ def create(lib, desc):
 
 @pytest.mark.parametrize("mutate,needle", [
     (lambda d: d.__setitem__("mass", np.array([0.0] + list(d["mass"][1:]))), "mass"),
-    (lambda d: d.__setitem__("dof", np.array([2] * len(d["dof"]), dtype=np.int32)), "dof"),
+    (lambda d: d.__setitem__("dof", np.array([4] * len(d["dof"]), dtype=np.int32)), "dof"),
     (lambda d: d.__setitem__("child", np.array([1] * len(d["child"]), dtype=np.int32)), "child"),
     (lambda d: d.__setitem__("act_axis", np.array([1] * len(d["act_axis"]), dtype=np.int32)), "act_axis"),
     (lambda d: d.__setitem__("pair_a", np.array([99] * len(d["pair_a"]), dtype=np.int32)), "pair"),

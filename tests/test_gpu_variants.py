@@ -14,7 +14,7 @@ from parity_util import decided_envs
 
 pytestmark = pytest.mark.gpu
 
-SCENES = ["quadruped_variants", "quadruped_planar"]
+SCENES = ["quadruped_variants", "quadruped_planar", "quadruped_2dof"]
 
 
 @pytest.fixture(scope="module")

@@ -862,3 +862,30 @@ def test_target_angle_actuator_converges_to_its_target():
         target = 0.5 * (lo + hi) + 0.5 * (hi - lo) * min(max(a, -1), 1)
         assert abs(orc.joint_angles(d, out)[0, 0] - target) < 1e-6, a
         assert np.abs(out[0, 1, 10:13]).max() < 1e-6
+
+
+def test_two_dof_joint_twist_spring_and_free_axes():
+    """2-DOF (universal) joint, READING: rotations about its two joint axes
+    meet no spring (inside the limits), the twist about the third axis is
+    held by a spring of the alignment stiffness k_a.  Frozen parent, child
+    centred on the anchor, g = 0, no damping; one substep from rest: a child
+    turned by 0.3 rad about the first axis stays at rest, a child twisted by
+    0.3 rad about the third axis gets w = -h k_a 0.3 / I along that axis."""
+    h, I, ka = 0.005, 0.5, 40.0
+    sb = S.SceneBuilder(dt=h, substeps=1, gravity=(0, 0, 0))
+    p = sb.body("P", 1.0, (1, 1, 1), (0, 0, 0), frozen_pos=(1, 1, 1), frozen_rot=(1, 1, 1))
+    cb = sb.body("C", 1.0, (I, I, I), (0, 0, 0))
+    sb.joint(p, cb, anchor=(0, 0, 0), axis=(1, 0, 0), ref=(0, 1, 0), dof=2, stiffness=10000.0,
+             spring_damping=0.0, angular_stiffness=ka, angular_damping=0.0, limits=((-60, 60), (-60, 60)),
+             limit_stiffness=50.0)
+    d = sb.build()
+    assert list(d["dof"]) == [2]
+    st = state_of(d)
+    st[0, 1, 3:7] = axis_angle([1, 0, 0], 0.3)  # about joint axis 0 (world x)
+    out = orc.rollout(d, st, np.zeros((1, 1, 0)))
+    assert np.abs(out[0, 1, 7:13]).max() < 1e-14
+    st[0, 1, 3:7] = axis_angle([0, 0, 1], 0.3)  # twist about the third axis (world z)
+    assert abs(orc.joint_angles(d, st)[0, 0]) < 1e-15
+    out = orc.rollout(d, st, np.zeros((1, 1, 0)))
+    assert np.allclose(out[0, 1, 10:13], [0.0, 0.0, -h * ka * 0.3 / I], atol=1e-14, rtol=0)
+    assert np.abs(out[0, 1, 7:10]).max() < 1e-14
