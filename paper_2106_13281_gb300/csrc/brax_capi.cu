@@ -941,7 +941,7 @@ int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     sg.ccount = contact_count;
     apply_env(s, sg, env);
     L.seg[0] = sg;
-    const size_t smem = s->pair_groups * pair_group_bytes(s->B);
+    const size_t smem = s->pair_groups * pair_group_bytes(s->B, s->A);
     const int threads = 32 * s->B * s->pair_groups;
     const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, T,
                                        pair_blocks_per_sm(s->pair_variant, threads, smem));

@@ -358,15 +358,41 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
   const int64_t N = sg.n_envs;
   const int64_t ea = ((int64_t)unit * sg.groups + g) * 64 + lane, eb = ea + 32;
   const bool va = ea < N, vb = eb < N;
-  GroupMem2 gm = group_mem2(reinterpret_cast<float*>(smem) + g * group_floats2(B), B);
+  GroupMem2 gm = group_mem2(reinterpret_cast<float*>(smem) + g * group_floats2(B, sg.A), B);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
   const BodyP2& q = bodies2[b];
+  // The group's actions come as one tile per step, [64 environments][A]
+  // (contiguous in the action array), brought into shared memory by a bulk
+  // asynchronous copy issued one step ahead by one thread and double-buffered;
+  // each body warp then reads its actuator's column.  A group whose tile is
+  // not 16-byte sized and aligned (a ragged last group, A * N not a multiple
+  // of 4) loads its actions directly.
+  const int64_t e0 = ((int64_t)unit * sg.groups + g) * 64;
+  const int64_t nv = N - e0 < 64 ? N - e0 : 64;
+  const uint32_t tile_bytes = nv > 0 ? (uint32_t)(nv * sg.A * 4) : 0u;
+  const bool use_tile = sg.A > 0 && nv > 0 && (tile_bytes & 15u) == 0 && ((N * sg.A) & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(sg.actions) & 15u) == 0;
+  const bool issuer = use_tile && b == 0 && lane == 0;
+  if (issuer) {
+    mbar_init(gm.mbar, 1);
+    mbar_init(gm.mbar + 1, 1);
+    fence_mbar_init();
+  }
   if (b == 0) {
     gm.cnt[lane] = 0;
     gm.cnt[32 + lane] = 0;
   }
-  if (sg.ccount) group_sync(bar, nthr);
+  if (sg.ccount || use_tile) group_sync(bar, nthr);
+  auto issue_tile = [&](int t) {  // the issuing thread: step t's tile into buffer (t - t0) & 1
+    const int i = (t - t0) & 1;
+    fence_proxy_async();  // this buffer's earlier reads (before the last barrier) precede the async write
+    bulk_copy_g2s(gm.tile + i * 64 * sg.A, sg.actions + ((int64_t)t * N + e0) * sg.A, tile_bytes, gm.mbar + i);
+  };
+  if (issuer) {
+    issue_tile(t0);
+    if (t0 + 1 < t1) issue_tile(t0 + 1);
+  }
   p2::Body s;
   {  // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
     const float* src = c == 0 ? sg.state0 : sg.state_T;
@@ -387,7 +413,16 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
       if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
     }
     f2 act = zero2();
-    if (has_parent && act_idx >= 0) {
+    if (use_tile) {
+      const int i = t - t0;
+      if (issuer && i > 0 && t + 1 < t1) issue_tile(t + 1);  // every warp has left step t - 1's buffer
+      if (has_parent && act_idx >= 0) {
+        if (!mbar_wait(gm.mbar + (i & 1), (uint32_t)((i >> 1) & 1), L.sc.wait_ns > 0 ? L.sc.wait_ns : 2000000000LL))
+          atomicOr(sg.status, kStatusTimeout);
+        const float* tl = gm.tile + (i & 1) * 64 * A + act_idx;
+        act = make_float2(va ? tl[lane * A] : 0.f, vb ? tl[(32 + lane) * A] : 0.f);
+      }
+    } else if (has_parent && act_idx >= 0) {
       const float* ap = sg.actions + (int64_t)t * N * A + act_idx;
       act = make_float2(va ? __ldg(ap + ea * A) : 0.f, vb ? __ldg(ap + eb * A) : 0.f);
     }
@@ -494,6 +529,11 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
       }
     }
     bad |= !finite_pair(s);
+  }
+  if (issuer) {  // no bulk copy may outlive the block: wait (bounded) for the last one into each buffer
+    const int n = t1 - t0;
+    for (int i = (n >= 2 ? n - 2 : 0); i < n; ++i)
+      if (!mbar_wait(gm.mbar + (i & 1), (uint32_t)((i >> 1) & 1), 2000000000LL)) atomicOr(sg.status, kStatusTimeout);
   }
   if (va) store_half(sg.state_T + (ea * B + b) * 13, s, 0);
   if (vb) store_half(sg.state_T + (eb * B + b) * 13, s, 1);
@@ -673,7 +713,7 @@ int pair_variant_max_threads(int variant) {
   static const int t[5] = {288, 576, 1024, 288, 864};
   return (variant >= 0 && variant < 5) ? t[variant] : 0;
 }
-size_t pair_group_bytes(int B) { return (size_t)p2::group_floats2(B) * sizeof(float); }
+size_t pair_group_bytes(int B, int A) { return (size_t)p2::group_floats2(B, A) * sizeof(float); }
 
 int rollout_variant_max_threads(int variant) {
   static const int t[4] = {384, 576, 1024, 288};

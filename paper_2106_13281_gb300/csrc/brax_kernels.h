@@ -25,7 +25,7 @@ cudaError_t launch_rollout_pair(const Launch& L, int grid, int threads, size_t s
 int pair_variant_max_threads(int variant);
 // Resident blocks per SM of a paired-kernel variant (0 if it cannot launch).
 int pair_blocks_per_sm(int variant, int threads, size_t smem);
-size_t pair_group_bytes(int B);
+size_t pair_group_bytes(int B, int A);
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
                                     cudaStream_t st);
 size_t backward_smem_bytes(int B, int P, int groups);

@@ -160,11 +160,19 @@ struct Acc {
 //                          for the contact response)
 constexpr int kPubFields2 = 18;
 constexpr int kReactFields2 = 12;
-__host__ __device__ inline int group_floats2(int B) { return 2 * 32 * B * (kPubFields2 + kReactFields2) + 64; }
+// then the contact counts [64] int, two mbarriers (8 bytes each) and the
+// group's action tile, double-buffered: [2][64 environments][A] floats (the
+// 64 environments are contiguous in the action array, so one bulk copy brings
+// a step's tile; every offset is a multiple of 16 bytes)
+__host__ __device__ inline int group_floats2(int B, int A) {
+  return 2 * 32 * B * (kPubFields2 + kReactFields2) + 64 + 4 + 2 * 64 * A;
+}
 struct GroupMem2 {
   f2* pub;
   f2* react;
-  int* cnt;  // [64] contact counts (A lanes, then B lanes)
+  int* cnt;        // [64] contact counts (A lanes, then B lanes)
+  uint64_t* mbar;  // [2] completion of the action tile's bulk copies
+  float* tile;     // [2][64][A] action tiles
   __device__ __forceinline__ f2* pubf(int b, int f) { return pub + (b * kPubFields2 + f) * 32; }
   __device__ __forceinline__ f2* reactf(int b, int f) { return react + (b * kReactFields2 + f) * 32; }
 };
@@ -173,7 +181,49 @@ __device__ __forceinline__ GroupMem2 group_mem2(float* base, int B) {
   m.pub = reinterpret_cast<f2*>(base);
   m.react = m.pub + B * kPubFields2 * 32;
   m.cnt = reinterpret_cast<int*>(m.react + B * kReactFields2 * 32);
+  m.mbar = reinterpret_cast<uint64_t*>(m.cnt + 64);
+  m.tile = reinterpret_cast<float*>(m.mbar + 2);
   return m;
+}
+
+// ------------------------------------------------------------------ action tile (bulk asynchronous copy)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One thread: expect `bytes` on m and copy them from global src to shared dst
+// (both 16-byte aligned, bytes a multiple of 16); the copy completes m's phase.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(m))
+      : "memory");
+}
+// Wait until m completes the phase of the given parity; gives up (returns
+// false) after wait_ns nanoseconds of the global timer.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int64_t wait_ns) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((int64_t)(t - t0) > wait_ns) return false;
+  }
 }
 
 // ------------------------------------------------------------------ phase K

@@ -38,7 +38,7 @@ def settled(d, N, seed, drop=0.0, T=20):
     return orc.rollout(d, st, a).astype(np.float32).astype(np.float64)
 
 
-CASES = [("quadruped", 0.38), ("biped", 0.0), ("pendulum", 0.0)]
+CASES = [("quadruped", 0.38), ("biped", 0.0), ("pendulum", 0.0), ("quadruped_2dof", 0.38)]
 
 
 @pytest.mark.parametrize("name,drop", CASES)
