@@ -329,6 +329,116 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);
 }
 
+// Whether the own plane-contact point is active (plane_point()'s test: the
+// sphere penetrates and the effective mass is positive).
+template <class PT>
+__device__ __forceinline__ int plane_point_active(const BodyP& bp, const PT& pt, const PlaneP& pl, const Body& s,
+                                                  const Frame& f) {
+  const V3 ro = mulc(f.R, pt.o);
+  const V3 n = ld3(pl.n);
+  const float depth = pt.r - dot((s.x + ro) - ld3(pl.p0), n);
+  if (!(depth > 0.f)) return 0;
+  return eff_mass(bp.flags, bp.inv_mass, f.Ii, fma3(-pt.r, n, ro), n) > 0.f ? 1 : 0;
+}
+
+// Reverse of one substep of a hinge-only system whose bodies all have
+// isotropic inertia.  Then I_w = R diag(c) R^T = c 1 for every R, so the
+// adjoint of I_w reaches no orientation (dI_w/dR = 0) and the summed force
+// and torque of the potential integrator, which only that adjoint reads, are
+// not needed: no joint is recomputed forward and no child reaction is read.
+// What is left needs two group barriers instead of four:
+//   K  kinematic + frame, publish; P: adjoints of F and tau -> gwr[b]
+//   -- barrier --
+//   J  joint (child side; parent adjoints -> gpub[b]), own plane contacts
+//   -- barrier --
+//   K  gather children's gpub, frame and kinematic integrator.
+// Shared memory: a parent's published state and gwr are written before the
+// first barrier and read between the two; gpub is written between them and
+// read after the second; the next substep writes each only after the
+// barrier that follows its last read.
+__device__ __forceinline__ void bwd_substep_iso(const SysP& S, const PlaneP* planes, const BodyP& bp,
+                                                const HingeRegs& hr, const PointRegs* pr, int b, int lane,
+                                                GroupMem& gm, BwdMem& bm, int bar, int nthr, const Body& s_in,
+                                                GBody& g, const float* act, float* gact) {
+  const float h = S.h;
+  Body s = s_in;
+  kinematic(bp, h, s);
+  const Frame f = make_frame(bp, s);
+  if (bp.flags & kPublish) publish<false>(gm, b, lane, s, f, bp);
+  // ---- reverse P: v1 = v + h (F/m + g), w1 = w + h Ii tau (+ contact updates)
+  V3 gv2 = g.v, gw2 = g.w;
+  if (bp.flags & kAnyFrozen) {
+    gv2 = mask3(bp.flags, gv2);
+    gw2 = mask3(bp.flags >> 3, gw2);
+  }
+  const V3 gFt = (h * bp.inv_mass) * gv2;
+  const V3 gTt = mul(f.Ii, h * gw2);
+  {
+    float* o = bm.gwr + (b * 6) * 32 + lane;
+    o[0] = gFt.x;
+    o[32] = gFt.y;
+    o[64] = gFt.z;
+    o[96] = gTt.x;
+    o[128] = gTt.y;
+    o[160] = gTt.z;
+  }
+  group_sync(bar, nthr);
+  // ---- reverse J
+  V3 gx1 = g.x, gvm = gv2, gwm = gw2;
+  M3 gR;
+  zero(gR);
+  if (bp.flags & kHasParent) {
+    const Pub pp = read_pub(gm, bp.parent, lane);
+    const float* pg = bm.gwr + (bp.parent * 6) * 32 + lane;
+    const V3 gFp = mk3(pg[0], pg[32], pg[64]);
+    const V3 gTp = mk3(pg[96], pg[128], pg[160]);
+    V3 gxp = zero3(), gvp = zero3(), gwp = zero3();
+    M3 gRp;
+    zero(gRp);
+    joint_hinge_bwd(hr, pp, s, f, act, gFt, gTt, gFp, gTp, gx1, gR, gvm, gwm, gxp, gRp, gvp, gwp, gact);
+    float* o = bm.gpub + (b * 18) * 32 + lane;
+    o[0] = gxp.x;
+    o[32] = gxp.y;
+    o[64] = gxp.z;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[(3 + i) * 32] = gRp.m[i];
+    o[12 * 32] = gvp.x;
+    o[13 * 32] = gvp.y;
+    o[14 * 32] = gvp.z;
+    o[15 * 32] = gwp.x;
+    o[16 * 32] = gwp.y;
+    o[17 * 32] = gwp.z;
+  }
+  const int np = bp.n_points;
+  int n = 0;
+  if (np > 0) n += plane_point_active(bp, pr[0], planes[bp.pt[0].plane], s, f);
+  if (np > 1) n += plane_point_active(bp, pr[1], planes[bp.pt[1].plane], s, f);
+  for (int i = 2; i < np; ++i) n += plane_point_active(bp, bp.pt[i], planes[bp.pt[i].plane], s, f);
+  if (n > 0) {
+    const float inv = (S.average && n > 1) ? __fdividef(1.f, (float)n) : 1.f;
+    const V3 gdv = inv * g.v, gdw = inv * g.w;
+    S6 gI;  // the adjoint of I_w, which reaches nothing here
+    zero(gI);
+    plane_point_bwd(S, bp, pr[0], planes[bp.pt[0].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+    if (np > 1) plane_point_bwd(S, bp, pr[1], planes[bp.pt[1].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+    for (int i = 2; i < np; ++i)
+      plane_point_bwd(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+  }
+  group_sync(bar, nthr);
+  // ---- reverse K
+  for (int c = 0; c < bp.n_children; ++c) {
+    const float* o = bm.gpub + (bp.children[c] * 18) * 32 + lane;
+    gx1 = gx1 + mk3(o[0], o[32], o[64]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gR.m[i] += o[(3 + i) * 32];
+    gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
+    gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
+  }
+  float gq1[4] = {g.q[0], g.q[1], g.q[2], g.q[3]};
+  qmat_bwd(s.qw, s.qx, s.qy, s.qz, gR, gq1);
+  g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);
+}
+
 // Reverse pass of a group of 32 environments: checkpoint segments last
 // first.  A block runs unit blockIdx.x over all segments or, under a chunked
 // schedule (Sched; chunk_steps counts segments, chunk 0 holds the last
@@ -481,8 +591,11 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
       for (int k = nsub - 1; k >= 0; --k) {
         Body sin;
         load_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, sin);
-        bwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bm, bar, nthr, sin, gs, act,
-                              gact);
+        if (!kGeneral && S.iso)
+          bwd_substep_iso(S, planes, bp, hr, pr, b, lane, gm, bm, bar, nthr, sin, gs, act, gact);
+        else
+          bwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bm, bar, nthr, sin, gs, act,
+                                gact);
         __syncwarp();
         discard_state_ws(ws_subs - lane + (int64_t)k * 13 * stride, stride, lane);
       }

@@ -441,6 +441,9 @@ std::vector<unsigned char> build_blob(const brax_desc& d, int* n_planes_out, int
   for (int b = 0; b < B; ++b)
     if (bodies[b].act_angle) S.variants = 1;
   if (S.variants) S.general = 1;
+  S.iso = 1;
+  for (int b = 0; b < S.B; ++b)
+    S.iso = S.iso && bodies[b].inv_I[0] == bodies[b].inv_I[1] && bodies[b].inv_I[1] == bodies[b].inv_I[2];
   const double h = (double)d.dt / d.substeps;
   S.h = (float)h;
   S.beta_h = (float)(d.baumgarte / h);

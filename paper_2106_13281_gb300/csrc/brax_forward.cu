@@ -367,11 +367,11 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
   // asynchronous copy issued one step ahead by one thread and double-buffered;
   // each body warp then reads its actuator's column.  A group whose tile is
   // not 16-byte sized and aligned (a ragged last group, A * N not a multiple
-  // of 4) loads its actions directly.
+  // of 4) loads its actions directly, and a launch of no steps copies none.
   const int64_t e0 = ((int64_t)unit * sg.groups + g) * 64;
   const int64_t nv = N - e0 < 64 ? N - e0 : 64;
   const uint32_t tile_bytes = nv > 0 ? (uint32_t)(nv * sg.A * 4) : 0u;
-  const bool use_tile = sg.A > 0 && nv > 0 && (tile_bytes & 15u) == 0 && ((N * sg.A) & 3) == 0 &&
+  const bool use_tile = t1 > t0 && sg.A > 0 && nv > 0 && (tile_bytes & 15u) == 0 && ((N * sg.A) & 3) == 0 &&
                         (reinterpret_cast<uintptr_t>(sg.actions) & 15u) == 0;
   const bool issuer = use_tile && b == 0 && lane == 0;
   if (issuer) {

@@ -120,6 +120,7 @@ struct SysP {
   int32_t n_parents;  // bodies with at least one child
   int32_t gyro;       // 1: the potential integrator adds the gyroscopic torque -w x (I_w w)
   int32_t variants;   // 1: damping, gyroscopic term or target-angle actuators (general kernel only)
+  int32_t iso;        // 1: every body's inertia is isotropic (I_w = I for every orientation)
 };
 
 // Two environments per thread (systems with hinge joints only and at most

@@ -223,7 +223,7 @@ class BraxSystem:
         first use) keeps the device workspace between calls.  Returns the
         number of rollout launches."""
         N, T = h_state0.shape[0], h_actions.shape[0]
-        if not (h_state0.is_pinned() and h_actions.is_pinned() and h_state_T.is_pinned()):
+        if not all(t.is_pinned() for t in (h_state0, h_actions, h_state_T) if t.numel()):
             raise ValueError("rollout_streamed: host tensors must be pinned")
         for t, shape, name in ((h_state0, (N, self.B, 13), "h_state0"), (h_actions, (T, N, self.A), "h_actions"),
                                (h_state_T, (N, self.B, 13), "h_state_T")):

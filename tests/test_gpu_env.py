@@ -127,3 +127,27 @@ def test_env_rollout_matches_oracle(brax, name, drop):
     nd = (obs.shape[2] - 11) // 2
     assert np.abs(obs[:, clear, 11:11 + nd] - obs_r[:, clear, 11:11 + nd]).max() < 1e-3
     assert np.abs(rew[:, clear] - rew_r[:, clear]).max() < 1e-2
+
+
+def test_env_rollout_edge_cases(brax):
+    """Zero steps return the state unchanged; without auto reset a done
+    environment keeps stepping from its own state (the physics of a plain
+    rollout), while its done flags and rewards are still written; min_z above
+    max_z is refused."""
+    from paper_2106_13281_gb300.binding import BraxError
+    d = S.quadruped()
+    sysm = brax(d)
+    N = 37
+    st = settled(d, N, 321, 0.38)
+    out = sysm.env_rollout(cuda(st), torch.zeros((0, N, sysm.A), device="cuda"))
+    assert torch.equal(out["state_T"], cuda(st))
+    a = S.actions(d, N, 6, 322)
+    z0 = st[:, 0, 2]
+    lo = float(np.quantile(z0, 0.5))
+    out = sysm.env_rollout(cuda(st), cuda(a), min_z=lo, max_z=10.0, auto_reset=False)
+    plain = sysm.rollout(cuda(st), cuda(a))["state_T"]
+    assert torch.equal(out["state_T"], plain)
+    assert out["done"].cpu().numpy().any()
+    with pytest.raises(BraxError):
+        sysm.env_rollout(cuda(st), cuda(a), min_z=1.0, max_z=0.5)
+    sysm.sync_status()

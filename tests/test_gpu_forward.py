@@ -393,3 +393,11 @@ def test_rollout_streamed_equals_one_launch(brax, name, drop):
             t, k = t + k, min(chunk, 2 * k)
         assert n == len(sizes), (chunk, first)
         assert torch.equal(out, ref), (chunk, first)
+    # zero steps: the state comes back unchanged
+    out.zero_()
+    assert sysm.rollout_streamed(hs, ha[:0].clone().pin_memory(), out, chunk_steps=10, bufs=bufs) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, hs)
+    # and so does a device rollout of zero steps (no action is read)
+    z = sysm.rollout(cuda(st), torch.zeros((0, N, sysm.A), device="cuda"))["state_T"]
+    assert torch.equal(z.cpu(), hs)
