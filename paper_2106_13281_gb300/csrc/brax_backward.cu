@@ -444,7 +444,7 @@ __device__ __forceinline__ void bwd_substep_iso(const SysP& S, const PlaneP* pla
 // schedule (Sched; chunk_steps counts segments, chunk 0 holds the last
 // ones), one chunk of the unit of the item it takes; the state adjoint then
 // passes from chunk to chunk through the workspace.
-template <bool kGeneral>
+template <bool kGeneral, bool kIso>
 __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -591,7 +591,7 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
       for (int k = nsub - 1; k >= 0; --k) {
         Body sin;
         load_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, sin);
-        if (!kGeneral && S.iso)
+        if (kIso)
           bwd_substep_iso(S, planes, bp, hr, pr, b, lane, gm, bm, bar, nthr, sin, gs, act, gact);
         else
           bwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bm, bar, nthr, sin, gs, act,
@@ -639,66 +639,39 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
 // Launch-bounds variants 0..3 (as the forward kernels), and variant 4: at
 // most 112 registers a thread (blocks of up to 576 threads; two 9-warp
 // groups per SM), which holds more of the adjoint's live values than the
-// 96 registers (576, 1) gives.
-template <int MAXT, int MINB, bool kGeneral>
+// 96 registers (576, 1) gives.  Each is compiled for three kinds of system:
+// hinge-only, hinge-only with isotropic inertia (bwd_substep_iso), general.
+template <int MAXT, int MINB, bool kGeneral, bool kIso>
 __global__ void __launch_bounds__(MAXT, MINB) rollout_bwd_kernel(const __grid_constant__ Launch L) {
-  rollout_bwd_body<kGeneral>(L);
+  rollout_bwd_body<kGeneral, kIso>(L);
 }
-template <bool kGeneral>
+template <bool kGeneral, bool kIso>
 __global__ void __maxnreg__(112) rollout_bwd_kernel_r112(const __grid_constant__ Launch L) {
-  rollout_bwd_body<kGeneral>(L);
+  rollout_bwd_body<kGeneral, kIso>(L);
 }
 
-template <class KernelT>
-static int bwd_occupancy_k(KernelT k, int threads, size_t smem) {
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
-  return n;
-}
-template <int MAXT, int MINB, bool G>
-static int bwd_occupancy_t(int threads, size_t smem) {
-  auto k = rollout_bwd_kernel<MAXT, MINB, G>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
-  return n;
-}
-int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem) {
-  if (variant == 4)
-    return general ? bwd_occupancy_k(rollout_bwd_kernel_r112<true>, threads, smem)
-                   : bwd_occupancy_k(rollout_bwd_kernel_r112<false>, threads, smem);
-  if (general) {
-    switch (variant) {
-      case 0: return bwd_occupancy_t<384, 2, true>(threads, smem);
-      case 1: return bwd_occupancy_t<576, 1, true>(threads, smem);
-      case 3: return bwd_occupancy_t<288, 3, true>(threads, smem);
-      default: return bwd_occupancy_t<1024, 1, true>(threads, smem);
-    }
-  }
+using BwdKernel = void (*)(const Launch);
+template <bool G, bool I>
+static BwdKernel bwd_kernel_t(int variant) {
   switch (variant) {
-    case 0: return bwd_occupancy_t<384, 2, false>(threads, smem);
-    case 1: return bwd_occupancy_t<576, 1, false>(threads, smem);
-    case 3: return bwd_occupancy_t<288, 3, false>(threads, smem);
-    default: return bwd_occupancy_t<1024, 1, false>(threads, smem);
+    case 0: return rollout_bwd_kernel<384, 2, G, I>;
+    case 1: return rollout_bwd_kernel<576, 1, G, I>;
+    case 3: return rollout_bwd_kernel<288, 3, G, I>;
+    case 4: return rollout_bwd_kernel_r112<G, I>;
+    default: return rollout_bwd_kernel<1024, 1, G, I>;
   }
 }
-
-template <int MAXT, int MINB, bool G>
-static cudaError_t launch_bwd_t(const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
-  auto k = rollout_bwd_kernel<MAXT, MINB, G>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, st>>>(L);
-  return cudaGetLastError();
+static BwdKernel bwd_kernel(int variant, bool general, bool iso) {
+  if (general) return bwd_kernel_t<true, false>(variant);
+  return iso ? bwd_kernel_t<false, true>(variant) : bwd_kernel_t<false, false>(variant);
 }
 
-template <class KernelT>
-static cudaError_t launch_bwd_k(KernelT k, const Launch& L, int grid, int threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, st>>>(L);
-  return cudaGetLastError();
+int backward_blocks_per_sm(int variant, bool general, bool iso, int threads, size_t smem) {
+  const BwdKernel k = bwd_kernel(variant, general, iso);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
+  return n;
 }
 
 int backward_variant_max_threads(int variant) {
@@ -707,24 +680,12 @@ int backward_variant_max_threads(int variant) {
 }
 
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
-                                    cudaStream_t st) {
-  if (variant == 4)
-    return general ? launch_bwd_k(rollout_bwd_kernel_r112<true>, L, grid, threads, smem, st)
-                   : launch_bwd_k(rollout_bwd_kernel_r112<false>, L, grid, threads, smem, st);
-  if (general) {
-    switch (variant) {
-      case 0: return launch_bwd_t<384, 2, true>(L, grid, threads, smem, st);
-      case 1: return launch_bwd_t<576, 1, true>(L, grid, threads, smem, st);
-      case 3: return launch_bwd_t<288, 3, true>(L, grid, threads, smem, st);
-      default: return launch_bwd_t<1024, 1, true>(L, grid, threads, smem, st);
-    }
-  }
-  switch (variant) {
-    case 0: return launch_bwd_t<384, 2, false>(L, grid, threads, smem, st);
-    case 1: return launch_bwd_t<576, 1, false>(L, grid, threads, smem, st);
-    case 3: return launch_bwd_t<288, 3, false>(L, grid, threads, smem, st);
-    default: return launch_bwd_t<1024, 1, false>(L, grid, threads, smem, st);
-  }
+                                    bool iso, cudaStream_t st) {
+  const BwdKernel k = bwd_kernel(variant, general, iso);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(L);
+  return cudaGetLastError();
 }
 
 cudaError_t upload_pool_backward(int off, const void* data, size_t bytes) {

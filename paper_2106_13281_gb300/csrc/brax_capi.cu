@@ -745,6 +745,7 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   s->A = S->A;
   s->D = S->D;
   s->general = S->general != 0;
+  s->iso = S->iso != 0;
   cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size());
   if (e != cudaSuccess) {
     delete s;
@@ -1329,10 +1330,12 @@ int rollout_backward_impl(const brax_system* s, int64_t n_envs, int32_t T, int32
   const size_t smem = backward_smem_bytes(s->B, s->P, 1);
   const int nseg = (T + K - 1) / K;
   const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, nseg,
-                                     backward_blocks_per_sm(variant, s->general, threads, smem), (16 + K - 1) / K);
+                                     backward_blocks_per_sm(variant, s->general, s->iso, threads, smem),
+                                     (16 + K - 1) / K);
   int64_t launch_grid;
   cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid, st, fr);
-  if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, threads, smem, variant, s->general, st);
+  if (e == cudaSuccess)
+    e = launch_rollout_backward(L, (int)launch_grid, threads, smem, variant, s->general, s->iso, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_rollout_backward");
 }
 }  // namespace
@@ -1365,7 +1368,7 @@ namespace {
 struct BwdBatchPlan {
   int grid = 0, threads = 0;
   size_t smem = 0, ws_bytes = 0;
-  bool general = false;
+  bool general = false, iso = true;
   std::vector<int> groups, cta_begin, cta_end;
   std::vector<size_t> ws_off;
 };
@@ -1388,6 +1391,7 @@ BwdBatchPlan plan_batch_backward(const brax_batch* b, int32_t K) {
     pl.ws_bytes += (wb + 255) & ~size_t(255);
     pl.smem = std::max(pl.smem, backward_smem_bytes(s->B, s->P, G));
     pl.general = pl.general || s->general;
+    pl.iso = pl.iso && s->iso;
   }
   pl.grid = cta;
   return pl;
@@ -1449,10 +1453,12 @@ extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32
   int device = 0;
   cudaGetDevice(&device);
   const SchedPlan sp = plan_schedule(b->sched_mode, b->sched_chunk, device, pl.grid, (T + K - 1) / K,
-                                     backward_blocks_per_sm(variant, pl.general, pl.threads, pl.smem), (16 + K - 1) / K);
+                                     backward_blocks_per_sm(variant, pl.general, pl.iso, pl.threads, pl.smem),
+                                     (16 + K - 1) / K);
   int64_t launch_grid;
   cudaError_t e = apply_schedule(sp, b->sched, 0, 2000000000LL, pl.grid, L, &launch_grid, st);
-  if (e == cudaSuccess) e = launch_rollout_backward(L, (int)launch_grid, pl.threads, pl.smem, variant, pl.general, st);
+  if (e == cudaSuccess)
+    e = launch_rollout_backward(L, (int)launch_grid, pl.threads, pl.smem, variant, pl.general, pl.iso, st);
   return e == cudaSuccess ? BRAX_OK : cuda_fail(e, "brax_batch_rollout_backward");
 }
 

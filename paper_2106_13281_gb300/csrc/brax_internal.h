@@ -27,6 +27,7 @@ struct SchedScratch {
 struct brax_system {
   int B = 0, A = 0, D = 0, P = 0, n_planes = 0;
   bool general = false;  // 3-DOF joints or body-body pairs present
+  bool iso = false;      // every body has isotropic inertia
   int device = 0;
   int pool_off = -1;     // offset of the blob in the constant parameter pool
   std::vector<unsigned char> blob;

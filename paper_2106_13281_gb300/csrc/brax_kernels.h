@@ -26,13 +26,15 @@ int pair_variant_max_threads(int variant);
 // Resident blocks per SM of a paired-kernel variant (0 if it cannot launch).
 int pair_blocks_per_sm(int variant, int threads, size_t smem);
 size_t pair_group_bytes(int B, int A);
+// iso: a hinge-only system whose bodies all have isotropic inertia (the
+// two-barrier reverse substep); ignored when general.
 cudaError_t launch_rollout_backward(const Launch& L, int grid, int threads, size_t smem, int variant, bool general,
-                                    cudaStream_t st);
+                                    bool iso, cudaStream_t st);
 size_t backward_smem_bytes(int B, int P, int groups);
 // Largest block of a reverse-kernel variant (0..3 as the forward; 4: 112 registers, up to 576 threads).
 int backward_variant_max_threads(int variant);
 // Resident blocks per SM of a reverse kernel variant (0 if it cannot launch).
-int backward_blocks_per_sm(int variant, bool general, int threads, size_t smem);
+int backward_blocks_per_sm(int variant, bool general, bool iso, int threads, size_t smem);
 int64_t backward_ws_floats_per_group(int B, int P, int K, int S);
 // fast_atan2 (and its packed form, out_packed) elementwise, for its accuracy test.
 cudaError_t launch_atan2_probe(const float* y, const float* x, float* out, float* out_packed, int64_t n,

@@ -449,6 +449,21 @@ def quadruped_variants() -> dict:
     return d
 
 
+def quadruped_aniso() -> dict:
+    """The quadruped with anisotropic inertias (torso and thighs) and nothing
+    else changed: a hinge-only system whose reverse pass must carry the
+    adjoint of the world inverse inertia I_w = R diag(1/I) R^T into the
+    orientation (Sec. 3), which isotropic bodies do not exercise."""
+    d = dict(quadruped())
+    inertia = np.array(d["inertia"], dtype=np.float64).copy()
+    inertia[0] = [0.8, 1.2, 1.6]
+    for b, name in enumerate(d["body_names"]):
+        if name.startswith("thigh"):
+            inertia[b] = [1.3, 0.9, 1.1]
+    d["inertia"] = inertia
+    return d
+
+
 def quadruped_2dof() -> dict:
     """The quadruped with 2-DOF (universal) hips: axis 0 swings the leg about
     the vertical (+-30 deg), axis 1 lifts it about the horizontal axis across
@@ -535,3 +550,4 @@ SCENES["capsule_in_box"] = lambda joint=None: capsule_on_box(True)
 SCENES["quadruped_variants"] = lambda joint=None: quadruped_variants()
 SCENES["quadruped_planar"] = lambda joint=None: planar(quadruped())
 SCENES["quadruped_2dof"] = lambda joint=None: quadruped_2dof()
+SCENES["quadruped_aniso"] = lambda joint=None: quadruped_aniso()

@@ -60,7 +60,7 @@ def rel_err(a, b):
 
 @pytest.mark.parametrize("name,drop,T", [("pendulum", 0.0, 5), ("quadruped", 0.38, 3), ("quadruped", 0.38, 10),
                                          ("biped", 0.0, 3), ("arm_box", 0.0, 3), ("capsule_on_box", 0.0, 1),
-                                         ("capsule_in_box", 0.0, 2)])
+                                         ("capsule_in_box", 0.0, 2), ("quadruped_aniso", 0.38, 3)])
 def test_adjoint_matches_oracle_tape(brax, name, drop, T):
     d = S.SCENES[name]()
     sysm = brax(d)
@@ -89,7 +89,7 @@ def test_adjoint_matches_oracle_tape(brax, name, drop, T):
 
 
 @pytest.mark.parametrize("name,drop", [("pendulum", 0.0), ("quadruped", 0.38), ("biped", 0.0), ("arm_box", 0.0),
-                                       ("capsule_on_box", 0.0), ("capsule_in_box", 0.0)])
+                                       ("capsule_on_box", 0.0), ("capsule_in_box", 0.0), ("quadruped_aniso", 0.38)])
 def test_single_substep_adjoint_exact(brax, name, drop):
     """One substep (dt = h): no trajectory divergence between FP32 and FP64
     can build up, so every environment's gradient matches the oracle tape
