@@ -97,7 +97,7 @@ __device__ __forceinline__ void store_body_ws(float* p, int stride, const Body& 
   p[12 * stride] = s.w.z;
 }
 
-template <bool kGeneral>
+template <bool kGeneral, bool kIso = false>
 __device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, const PairP* pairs,
                                             const PlaneP* planes, const BodyP& bp, const HingeRegs& hr,
                                             const PointRegs* pr, int b, int B, int lane, GroupMem& gm, int bar,
@@ -122,7 +122,7 @@ __device__ __forceinline__ void fwd_substep(const SysP& S, const BodyP* bodies, 
     for (int k = b; k < S.P; k += B) pair_forward(S, bodies, pairs[k], gm, k, lane);
   } else {
     plane_points_regs(S, bp, pr, planes, np < 2 ? np : 2, s, f, acc);
-    for (int i = 2; i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
+    for (int i = 2; !kIso && i < np; ++i) plane_point(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, acc);
   }
   group_sync(bar, nthr);
   integrate<kGeneral>(S, bp, gm, lane, s, f, wr, acc);
@@ -329,6 +329,18 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
   g = kinematic_bwd(bp, h, s_in, gx1, gq1, gvm, gwm);
 }
 
+// Register-resident contact point i (0 or 1) of the own body.
+__device__ __forceinline__ PointRegs sel_point(int i, const PointRegs* pr) {
+  PointRegs p;
+  p.o[0] = i ? pr[1].o[0] : pr[0].o[0];
+  p.o[1] = i ? pr[1].o[1] : pr[0].o[1];
+  p.o[2] = i ? pr[1].o[2] : pr[0].o[2];
+  p.r = i ? pr[1].r : pr[0].r;
+  p.mu = i ? pr[1].mu : pr[0].mu;
+  p.e = i ? pr[1].e : pr[0].e;
+  return p;
+}
+
 // Whether the own plane-contact point is active (plane_point()'s test: the
 // sphere penetrates and the effective mass is positive).
 template <class PT>
@@ -409,20 +421,20 @@ __device__ __forceinline__ void bwd_substep_iso(const SysP& S, const PlaneP* pla
     o[16 * 32] = gwp.y;
     o[17 * 32] = gwp.z;
   }
+  // own plane contacts: at most two points a body in this kind of system,
+  // both register-resident; one copy of each loop body
   const int np = bp.n_points;
   int n = 0;
-  if (np > 0) n += plane_point_active(bp, pr[0], planes[bp.pt[0].plane], s, f);
-  if (np > 1) n += plane_point_active(bp, pr[1], planes[bp.pt[1].plane], s, f);
-  for (int i = 2; i < np; ++i) n += plane_point_active(bp, bp.pt[i], planes[bp.pt[i].plane], s, f);
+#pragma unroll 1
+  for (int i = 0; i < np; ++i) n += plane_point_active(bp, sel_point(i, pr), planes[bp.pt[i].plane], s, f);
   if (n > 0) {
     const float inv = (S.average && n > 1) ? __fdividef(1.f, (float)n) : 1.f;
     const V3 gdv = inv * g.v, gdw = inv * g.w;
     S6 gI;  // the adjoint of I_w, which reaches nothing here
     zero(gI);
-    plane_point_bwd(S, bp, pr[0], planes[bp.pt[0].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
-    if (np > 1) plane_point_bwd(S, bp, pr[1], planes[bp.pt[1].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
-    for (int i = 2; i < np; ++i)
-      plane_point_bwd(S, bp, bp.pt[i], planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
+#pragma unroll 1
+    for (int i = 0; i < np; ++i)
+      plane_point_bwd(S, bp, sel_point(i, pr), planes[bp.pt[i].plane], s, f, gdv, gdw, gx1, gR, gI, gvm, gwm);
   }
   group_sync(bar, nthr);
   // ---- reverse K
@@ -570,7 +582,7 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
       if (t + 1 < t1) {
         load_act(t);
         for (int k = 0; k < nsub; ++k)
-          fwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
+          fwd_substep<kGeneral, kIso>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
       }
     }
     for (int t = t1 - 1; t >= t0; --t) {
@@ -581,7 +593,7 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
       for (int k = 0; k < nsub; ++k) {
         store_body_ws(ws_subs + (int64_t)k * 13 * stride, stride, s);
         if (k + 1 < nsub)
-          fwd_substep<kGeneral>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
+          fwd_substep<kGeneral, kIso>(S, bodies, pairs, planes, bp, hr, pr, b, B, lane, gm, bar, nthr, s, act);
       }
       if (sg.g_torso && b == 0 && valid) {
         const float* gt = sg.g_torso + ((int64_t)t * N + env) * 3;

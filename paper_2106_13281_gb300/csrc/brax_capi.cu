@@ -745,7 +745,10 @@ int brax_system_create(const brax_desc* desc, brax_system** out) {
   s->A = S->A;
   s->D = S->D;
   s->general = S->general != 0;
+  // the isotropic reverse kernel keeps at most two contact points a body in registers
   s->iso = S->iso != 0;
+  for (int b = 0; b < S->B; ++b)
+    if (reinterpret_cast<const BodyP*>(s->blob.data() + blob_bodies_off())[b].n_points > 2) s->iso = false;
   cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size());
   if (e != cudaSuccess) {
     delete s;
