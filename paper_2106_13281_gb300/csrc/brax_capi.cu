@@ -583,6 +583,17 @@ int pick_variant(int threads) {
     if (threads <= rollout_variant_max_threads(v)) return v;
   return -1;
 }
+// The reverse kernel's default launch (before any autotuning): the adjoint
+// holds more live values than the forward, so the largest register budget
+// whose block fits, (576, 1) or (1024, 1); the tighter bounds spill more than
+// the extra resident blocks hide (quadruped reverse, 65,536 x 100: 53 ms
+// under (288, 3), 41 ms under (576, 1)).
+int pick_bwd_variant(int threads) {
+  static const int order[2] = {1, 2};
+  for (int v : order)
+    if (threads <= backward_variant_max_threads(v)) return v;
+  return -1;
+}
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -1328,7 +1339,8 @@ int rollout_backward_impl(const brax_system* s, int64_t n_envs, int32_t T, int32
   L.seg[0] = sg;
   const int threads = 32 * s->B;
   const int variant =
-      (s->bwd_variant >= 0 && threads <= backward_variant_max_threads(s->bwd_variant)) ? s->bwd_variant : pick_variant(threads);
+      (s->bwd_variant >= 0 && threads <= backward_variant_max_threads(s->bwd_variant)) ? s->bwd_variant
+                                                                                        : pick_bwd_variant(threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout_backward: system too large for one block");
   const size_t smem = backward_smem_bytes(s->B, s->P, 1);
   const int nseg = (T + K - 1) / K;
@@ -1451,7 +1463,7 @@ extern "C" int brax_batch_rollout_backward(const brax_batch* b, int32_t T, int32
     sg.ws = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + pl.ws_off[i]);
     L.seg[i] = sg;
   }
-  const int variant = pick_variant(pl.threads);
+  const int variant = pick_bwd_variant(pl.threads);
   if (variant < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_batch_rollout_backward: block too large");
   int device = 0;
   cudaGetDevice(&device);
