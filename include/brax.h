@@ -171,11 +171,11 @@ int brax_step(const brax_system* sys, int64_t n_envs, const float* state_in, con
  *   torso_traj    [T, N, 3]: body 0's position after every step;
  *   contact_count [N] int32: active contacts summed over all substeps.
  * Systems with hinge joints only and at most two plane-contact points per
- * body run two environments per thread (packed FP32x2 arithmetic) when no
- * checkpoints are requested; a rollout that writes checkpoints runs the
- * one-environment kernel, whose arithmetic brax_rollout_backward recomputes
- * with, so gradients do not depend on K.  The two kernels agree to FP32
- * rounding.
+ * body run two environments per thread (packed FP32x2 arithmetic) unless the
+ * autotuner found the one-environment kernel faster; checkpointing rollouts
+ * run the same kernel, and brax_rollout_backward rebuilds step states with
+ * the kernel that wrote the checkpoints, so gradients do not depend on K.
+ * The two kernels agree to FP32 rounding.
  * Schedule: a block keeps its environments on chip for the whole rollout,
  * so when the blocks are not a whole number of resident waves the last wave
  * would run part-empty from the first step to the last.  Then the rollout of
@@ -264,7 +264,10 @@ int brax_rollout_streamed(const brax_system* sys, int64_t n_envs, int32_t T, con
                           const float* h_actions, float* h_state_T, int32_t chunk_steps, int32_t first_steps,
                           void* workspace, size_t workspace_bytes, void* stream);
 
-/* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K). */
+/* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K).
+ * The figure depends on the system's current forward kernel (a system on
+ * the two-environments kernel with K > 1 also holds one checkpoint segment
+ * of step states), so ask again after brax_autotune. */
 int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, size_t* bytes);
 
 /* Reverse-mode gradient of a rollout (the differentiable step, Sec. 1 and
@@ -272,7 +275,10 @@ int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32
  * brax_rollout with the same K; cotangents g_state_T [N,B,13] (required)
  * and g_torso_traj [T,N,3] (NULL = zero).  Outputs g_actions [T,N,A] and
  * g_state0 [N,B,13] (either may be NULL).  The forward is recomputed from
- * each checkpoint segment on chip.  workspace: device scratch of at least
+ * each checkpoint segment on chip; on a system whose checkpoints come from
+ * the two-environments kernel and K > 1, that kernel first rebuilds the
+ * segment's step states into the workspace (one forward launch and one
+ * reverse launch a segment, last segment first).  workspace: device scratch of at least
  * brax_workspace_size bytes, 256-byte aligned.  When the blocks do not fill
  * a whole number of resident waves the launch takes the chunked schedule of
  * brax_rollout over checkpoint segments (last first), with the same scratch

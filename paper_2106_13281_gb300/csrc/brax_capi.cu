@@ -928,7 +928,7 @@ void apply_env(const brax_system* s, Seg& sg, const EnvOut* env) {
 
 int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, const float* state0,
                  const float* actions, float* state_T, float* checkpoints, float* torso_traj, int32_t* contact_count,
-                 void* stream, const EnvOut* env) {
+                 void* stream, const EnvOut* env, const FixedRegion& fr = FixedRegion{}) {
   if (!s || n_envs < 0 || T < 0) return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: bad arguments");
   if (n_envs > 0 && (!state0 || !state_T || (T > 0 && s->A > 0 && !actions)))
     return fail(BRAX_ERR_INVALID_ARGUMENT, "brax_rollout: null state or actions");
@@ -940,11 +940,11 @@ int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   L.n_segs = 1;
   L.T = T;
   L.K = K < 1 ? 1 : K;
-  // Two environments per thread for plain forward rollouts.  A rollout that
-  // writes checkpoints feeds the reverse pass, which recomputes the substeps
-  // between checkpoints with the one-environment arithmetic: it runs that
-  // kernel too, so gradients do not depend on the checkpoint interval.
-  if (s->pair_mode == 1 && !checkpoints) {
+  // Two environments per thread whenever the system has that kernel and it
+  // is switched on, checkpointing rollouts included: the reverse pass then
+  // rebuilds a checkpoint segment's step states with this same kernel
+  // (rollout_backward_impl), so gradients do not depend on K.
+  if (s->pair_mode == 1) {
     Seg sg = make_seg(s, s->pair_groups, n_envs);
     const int64_t per_cta = 64LL * s->pair_groups;
     const int64_t grid = (n_envs + per_cta - 1) / per_cta;
@@ -959,13 +959,25 @@ int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
     sg.ccount = contact_count;
     apply_env(s, sg, env);
     L.seg[0] = sg;
-    const size_t smem = s->pair_groups * pair_group_bytes(s->B, s->A);
+    size_t smem = s->pair_groups * pair_group_bytes(s->B, s->A);
+    if (checkpoints) {  // checkpoint staging buffers, [64][B][13] floats a group, when they fit
+      const size_t with = smem + (size_t)s->pair_groups * 64 * s->B * 13 * sizeof(float);
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 0;
+      }
+      if (with + 1024 <= (size_t)optin) {
+        smem = with;
+        L.seg[0].ck_stage = 1;
+      }
+    }
     const int threads = 32 * s->B * s->pair_groups;
     const SchedPlan pl = plan_schedule(s->sched_mode, s->sched_chunk, s->device, grid, T,
                                        pair_blocks_per_sm(s->pair_variant, threads, smem));
     int64_t launch_grid;
     cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
-                                   as_stream(stream));
+                                   as_stream(stream), fr);
     s->last_grid = launch_grid;
     s->last_chunks = L.sc.n_chunks;
     s->last_chunk_steps = L.sc.chunk_steps;
@@ -994,7 +1006,7 @@ int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
                                      rollout_blocks_per_sm(s->variant, s->general, threads, smem));
   int64_t launch_grid;
   cudaError_t e = apply_schedule(pl, s->sched, s->sched_first, s->sched_wait_ns, grid, L, &launch_grid,
-                                 as_stream(stream));
+                                 as_stream(stream), fr);
   s->last_grid = launch_grid;
   s->last_chunks = L.sc.n_chunks;
   s->last_chunk_steps = L.sc.chunk_steps;
@@ -1273,10 +1285,25 @@ namespace {
 // One group of 32 environments per block for the reverse kernel.
 int64_t bwd_groups_total(int64_t n_envs) { return (n_envs + 31) / 32; }
 
-size_t bwd_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
+// Scratch of the reverse kernel proper for (n_envs, K).
+size_t bwd_kernel_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
   const SysP* S = reinterpret_cast<const SysP*>(s->blob.data());
   return (size_t)bwd_groups_total(n_envs) * (size_t)backward_ws_floats_per_group(s->B, s->P, K, S->substeps) *
          sizeof(float);
+}
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+// Whether the reverse pass rebuilds each checkpoint segment's step states
+// with the two-environments kernel (the one that wrote the checkpoints)
+// instead of recomputing them inside the reverse kernel.
+bool bwd_by_segments(const brax_system* s, int32_t K) { return s->pair_mode == 1 && K > 1; }
+// Scratch of brax_rollout_backward for (n_envs, K), K already at most T.
+// Rebuilding segments: the reverse kernel's scratch for K = 1, the step
+// states of one segment [K][N][B][13] and two state adjoints [N][B][13]
+// passed from segment to segment.
+size_t bwd_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
+  if (!bwd_by_segments(s, K)) return bwd_kernel_ws_bytes(s, n_envs, K);
+  const size_t st = (size_t)n_envs * s->B * 13 * sizeof(float);
+  return align256(bwd_kernel_ws_bytes(s, n_envs, 1)) + align256((size_t)K * st) + 2 * align256(st);
 }
 
 }  // namespace
@@ -1318,6 +1345,45 @@ int rollout_backward_impl(const brax_system* s, int64_t n_envs, int32_t T, int32
     return fail(BRAX_ERR_WORKSPACE, "brax_rollout_backward: workspace missing or smaller than brax_workspace_size");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
     return fail(BRAX_ERR_WORKSPACE, "brax_rollout_backward: workspace must be 256-byte aligned");
+  if (bwd_by_segments(s, Ke)) {
+    // Checkpoint segments, last first: the two-environments kernel (which
+    // wrote the checkpoints) rebuilds the segment's step states from its
+    // checkpoint, K - 1 steps with a checkpoint every step plus the state
+    // after them; then the reverse kernel runs the segment with K = 1 and
+    // hands its state adjoint to the next segment.  Bitwise the same step
+    // states as the forward, so the gradients do not depend on K.
+    const size_t sb = (size_t)n_envs * s->B * 13 * sizeof(float);
+    const size_t kern = align256(bwd_kernel_ws_bytes(s, n_envs, 1));
+    unsigned char* base = static_cast<unsigned char*>(workspace);
+    float* steps = reinterpret_cast<float*>(base + kern);
+    float* carry[2] = {reinterpret_cast<float*>(base + kern + align256((size_t)Ke * sb)),
+                       reinterpret_cast<float*>(base + kern + align256((size_t)Ke * sb) + align256(sb))};
+    const size_t per_state = (size_t)n_envs * s->B * 13, per_act = (size_t)n_envs * s->A;
+    const int nseg = (T + K - 1) / K;
+    const float* g_in = g_state_T;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+      const int t0 = sgi * K, len = std::min(K, T - t0);
+      const float* ck = checkpoints + (size_t)sgi * per_state;
+      const float* act = actions ? actions + (size_t)t0 * per_act : nullptr;
+      int rc = BRAX_OK;
+      if (len > 1) {
+        rc = rollout_impl(s, n_envs, len - 1, 1, ck, act, steps + (size_t)(len - 1) * per_state, steps, nullptr,
+                          nullptr, stream, nullptr, fr);
+      } else {
+        cudaError_t e = cudaMemcpyAsync(steps, ck, sb, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "brax_rollout_backward");
+      }
+      if (rc != BRAX_OK) return rc;
+      float* g_out = sgi == 0 ? g_state0 : carry[sgi & 1];
+      rc = rollout_backward_impl(s, n_envs, len, 1, ck, act, steps, g_in,
+                                 g_torso_traj ? g_torso_traj + (size_t)t0 * n_envs * 3 : nullptr,
+                                 g_actions ? g_actions + (size_t)t0 * per_act : nullptr, g_out, workspace, kern, stream,
+                                 fr);
+      if (rc != BRAX_OK) return rc;
+      g_in = g_out;
+    }
+    return BRAX_OK;
+  }
   Launch L;
   std::memset(&L, 0, sizeof(L));
   L.n_segs = 1;

@@ -41,6 +41,7 @@ struct Seg {
   int32_t obs_dim, auto_reset;
   float fwd_w_dt;             // forward_weight / dt
   float healthy, ctrl_cost, min_z, max_z;
+  int32_t ck_stage;  // 1: the paired kernel stages checkpoints in shared memory (after its groups)
   // backward
   const float* g_state_T;
   const float* g_torso;

@@ -393,6 +393,11 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
     issue_tile(t0);
     if (t0 + 1 < t1) issue_tile(t0 + 1);
   }
+  // checkpoint staging buffer of this group, [64 environments][B][13] floats,
+  // after the groups' shared memory (sg.ck_stage)
+  float* stage = sg.ck_stage ? reinterpret_cast<float*>(smem) + sg.groups * group_floats2(B, sg.A) + g * 64 * B * 13
+                             : nullptr;
+  bool staged = false;  // this thread issued a bulk store of a staged checkpoint
   p2::Body s;
   {  // chunk 0 starts from state0, a later chunk from what the previous one left in state_T
     const float* src = c == 0 ? sg.state0 : sg.state_T;
@@ -409,8 +414,29 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
   for (int t = t0; t < t1; ++t) {
     if (sg.ckpt && (t % K) == 0) {
       float* ck = sg.ckpt + ((int64_t)(t / K) * N) * B * 13;
-      if (va) store_half(ck + (ea * B + b) * 13, s, 0);
-      if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
+      // The group's environments are one contiguous block of the checkpoint
+      // ([N][B][13]): every thread leaves its two states in the group's
+      // staging buffer and one thread stores the block with one bulk
+      // asynchronous copy, in place of 26 scattered 4-byte stores a thread.
+      // A block not 16-byte sized and aligned is stored directly.
+      float* dst = ck + e0 * B * 13;
+      const uint32_t ck_bytes = (uint32_t)(nv * B * 13) * 4u;
+      if (stage && nv > 0 && (ck_bytes & 15u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        store_half(stage + (lane * B + b) * 13, s, 0);
+        store_half(stage + ((32 + lane) * B + b) * 13, s, 1);
+        fence_proxy_async();  // the staged states, written by this thread, precede the bulk read
+        group_sync(bar, nthr);
+        if (b == 0 && lane == 0) {
+          // the buffer is written again only after the next group barrier,
+          // which this thread reaches once the copy has read it
+          bulk_copy_s2g(dst, stage, ck_bytes);
+          bulk_wait_read();
+          staged = true;
+        }
+      } else {
+        if (va) store_half(ck + (ea * B + b) * 13, s, 0);
+        if (vb) store_half(ck + (eb * B + b) * 13, s, 1);
+      }
     }
     f2 act = zero2();
     if (use_tile) {
@@ -530,6 +556,7 @@ __global__ void __launch_bounds__(MAXT, MINB) rollout_pair_kernel(const __grid_c
     }
     bad |= !finite_pair(s);
   }
+  if (staged) bulk_wait_all();  // the checkpoint stores are complete before the block ends
   if (issuer) {  // no bulk copy may outlive the block: wait (bounded) for the last one into each buffer
     const int n = t1 - t0;
     for (int i = (n >= 2 ? n - 2 : 0); i < n; ++i)

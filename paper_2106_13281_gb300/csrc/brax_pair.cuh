@@ -208,6 +208,20 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_addr(m))
       : "memory");
 }
+// One thread: store `bytes` from shared src to global dst (both 16-byte
+// aligned, bytes a multiple of 16) as one bulk asynchronous copy, committed
+// as a bulk group of its own.
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until the calling thread's bulk stores have read their shared sources
+// (a store from shared to this GPU's memory always finishes).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until the calling thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Wait until m completes the phase of the given parity; gives up (returns
 // false) after wait_ns nanoseconds of the global timer.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int64_t wait_ns) {

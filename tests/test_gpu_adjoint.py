@@ -178,17 +178,22 @@ def test_adjoint_vs_fp64_central_differences(brax):
             assert abs(fd[n] - g) <= 1e-3 * max(abs(fd[n]), abs(g)) + 1e-12, (b, j, n, fd[n], g)
 
 
-def test_checkpoint_interval_does_not_change_gradients(brax):
-    """Recomputation from checkpoints is exact: K = 1, 4 and T give bitwise
-    identical gradients (the forward is deterministic)."""
+@pytest.mark.parametrize("paired", [True, False])
+def test_checkpoint_interval_does_not_change_gradients(brax, paired):
+    """Recomputation from checkpoints is exact: K = 1, 4, 5 and T give
+    bitwise identical gradients (the forward is deterministic), whichever
+    kernel writes the checkpoints: the two-environments kernel (whose
+    segments the reverse pass rebuilds with the same kernel) or the
+    one-environment kernel (recomputed inside the reverse kernel)."""
     d = S.quadruped()
     sysm = brax(d)
+    sysm.set_pair_launch(1 if paired else 0, 1, 0)
     N, T = 33, 12
     st = settled(d, N, 31, 0.38)
     a = S.actions(d, N, T, 32)
     gT = np.random.default_rng(33).normal(size=st.shape)
     ref = None
-    for K in (1, 4, T):
+    for K in (1, 4, 5, T):
         ga, gs, _ = gpu_grad(sysm, st, a, gT, None, K)
         if ref is None:
             ref = (ga, gs)

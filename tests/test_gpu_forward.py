@@ -200,8 +200,8 @@ def test_checkpoints_and_torso(brax):
     ck, tor = out["checkpoints"], out["torso"]
     assert ck.shape[0] == math.ceil(T / K)
     assert torch.equal(ck[0], cuda(st))
-    # a checkpointing rollout runs the one-environment kernel (the arithmetic
-    # the reverse pass recomputes with): compare with rollouts of that kernel
+    # a checkpointing rollout runs the system's forward kernel (the one the
+    # reverse pass rebuilds segments with): compare with rollouts of it
     for k in range(1, ck.shape[0]):
         part = sysm.rollout(cuda(st), a[:k * K].contiguous(), K=k * K, checkpoints=True)["state_T"]
         assert torch.equal(ck[k], part)
@@ -334,8 +334,9 @@ def test_chunked_schedule_one_env_kernel(brax, name, drop):
         assert torch.equal(outs[0][k], outs[1][k]), k
 
 
+@pytest.mark.parametrize("paired", [True, False])
 @pytest.mark.parametrize("checkpoints", [False, True])
-def test_schedule_wait_gives_up_with_timeout_status(brax, checkpoints):
+def test_schedule_wait_gives_up_with_timeout_status(brax, checkpoints, paired):
     """The bounded wait of the chunked schedule: when the counter starts past
     chunk 0, every item waits for a flag that nothing sets; after 1 ms each
     block gives up, the status reads BRAX_ERR_TIMEOUT (6), and the context
@@ -346,9 +347,11 @@ def test_schedule_wait_gives_up_with_timeout_status(brax, checkpoints):
     N, T = 100, 10
     st, _ = initial(d, N, 25, drop=0.38)
     st, a = cuda(st), cuda(S.actions(d, N, T, 26))
-    sysm.set_pair_launch(1, 1, 0)
-    units = (N + 63) // 64
-    if checkpoints:  # the one-environment kernel: blocks of 32 environments
+    if paired:  # two environments a thread: blocks of 64 environments
+        sysm.set_pair_launch(1, 1, 0)
+        units = (N + 63) // 64
+    else:  # the one-environment kernel: blocks of 32 environments
+        sysm.set_pair_launch(0, 1, 0)
         units = (N + 31) // 32
     sysm.set_schedule(2, 3, units, 1_000_000)
     sysm.rollout(st, a, checkpoints=checkpoints)
