@@ -264,21 +264,21 @@ int brax_rollout_streamed(const brax_system* sys, int64_t n_envs, int32_t T, con
                           const float* h_actions, float* h_state_T, int32_t chunk_steps, int32_t first_steps,
                           void* workspace, size_t workspace_bytes, void* stream);
 
-/* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K).
- * The figure depends on the system's current forward kernel (a system on
- * the two-environments kernel with K > 1 also holds one checkpoint segment
- * of step states), so ask again after brax_autotune. */
+/* Bytes of device scratch brax_rollout_backward needs for (n_envs, T, K):
+ * the reverse kernel's scratch and, when K > 1, one checkpoint segment of
+ * step states [K][N][B][13] and two state adjoints. */
 int brax_workspace_size(const brax_system* sys, int64_t n_envs, int32_t T, int32_t K, size_t* bytes);
 
 /* Reverse-mode gradient of a rollout (the differentiable step, Sec. 1 and
  * Sec. 5 APG).  Inputs: state0, actions and the checkpoints written by
  * brax_rollout with the same K; cotangents g_state_T [N,B,13] (required)
  * and g_torso_traj [T,N,3] (NULL = zero).  Outputs g_actions [T,N,A] and
- * g_state0 [N,B,13] (either may be NULL).  The forward is recomputed from
- * each checkpoint segment on chip; on a system whose checkpoints come from
- * the two-environments kernel and K > 1, that kernel first rebuilds the
- * segment's step states into the workspace (one forward launch and one
- * reverse launch a segment, last segment first).  workspace: device scratch of at least
+ * g_state0 [N,B,13] (either may be NULL).  With K > 1 the forward kernel
+ * that wrote the checkpoints rebuilds each segment's step states into the
+ * workspace (one forward launch and one reverse launch a segment, last
+ * segment first); the substeps of every step are recomputed on chip.  The
+ * gradients are bitwise the same for every K and every run.  workspace:
+ * device scratch of at least
  * brax_workspace_size bytes, 256-byte aligned.  When the blocks do not fill
  * a whole number of resident waves the launch takes the chunked schedule of
  * brax_rollout over checkpoint segments (last first), with the same scratch

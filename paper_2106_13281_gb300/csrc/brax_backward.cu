@@ -8,15 +8,19 @@
 //   subs   [S][13][B][32]  states at the start of every substep of one step
 //                          (recomputed from that step's state);
 //   slots  [P][8][32]      body-body pair impulses of the current substep
-//                          (systems with pairs only).
+//                          (systems with pairs only);
+//   pairg  [P][2][18][32]  each pair's adjoints of its two bodies' x1, R,
+//                          v, w, gathered by the bodies in a fixed order.
 // The reverse of a substep recomputes its forward intermediates (two group
 // barriers, as in the forward), then runs the adjoint in reverse order:
 //   P  potential + collision integrators          -> gwr[b] (dL/dF, dL/dtau)
 //   -- barrier --
 //   J  joint (child side; parent adjoints -> gpub[b]), own plane contacts,
-//      owned pairs (adjoints added to gpair[] of both bodies)
+//      owned pairs (their adjoints of both bodies to pairg in the workspace)
 //   -- barrier --
-//   K  gather children's gpub and gpair, frame and kinematic integrator.
+//   K  gather children's gpub and the own pairs' pairg (in the body's pair
+//      order, so the sums do not depend on warp timing), frame and kinematic
+//      integrator.
 // Every thread of a group holds one (body, environment) and its 13-float
 // adjoint in registers for the whole reverse sweep.
 #include <cuda_runtime.h>
@@ -36,17 +40,21 @@ __constant__ __align__(16) unsigned char c_pool[kPoolBytes];
 
 // Backward shared memory of one group (floats), after the forward layout.
 __host__ __device__ inline int bwd_extra_floats(int B, int P) {
-  return B * 6 * 32 + B * 18 * 32 + (P > 0 ? B * 6 * 32 + B * 18 * 32 : 0);
+  return B * 6 * 32 + B * 18 * 32 + (P > 0 ? B * 6 * 32 : 0);
 }
 __host__ __device__ inline int bwd_fwd_floats(int B, int P, bool slots_in_smem) {
   return B * kPubFields * 32 + B * kReactFields * 32 + (slots_in_smem ? P * kSlotFields * 32 : 0) + 32;
 }
 __host__ __device__ inline int bwd_group_floats(int B, int P) { return bwd_fwd_floats(B, P, false) + bwd_extra_floats(B, P); }
 // Workspace of one group: step states [K][13][B][32], substep states
-// [S][13][B][32], pair slots [P][kSlotFields][32], and the state adjoint
-// carried from one chunk of a chunked schedule to the next [13][B][32].
-__host__ __device__ inline int64_t ws_carry_off(int B, int P, int K, int S) {
+// [S][13][B][32], pair slots [P][kSlotFields][32], pair adjoints
+// [P][2][18][32], and the state adjoint carried from one chunk of a chunked
+// schedule to the next [13][B][32].
+__host__ __device__ inline int64_t ws_pairg_off(int B, int P, int K, int S) {
   return (int64_t)(K + S) * 13 * B * 32 + (int64_t)P * kSlotFields * 32;
+}
+__host__ __device__ inline int64_t ws_carry_off(int B, int P, int K, int S) {
+  return ws_pairg_off(B, P, K, S) + (int64_t)P * 2 * 18 * 32;
 }
 __host__ __device__ inline int64_t ws_group_floats(int B, int P, int K, int S) {
   return ws_carry_off(B, P, K, S) + (int64_t)13 * B * 32;
@@ -56,7 +64,7 @@ struct BwdMem {
   float* gwr;    // [B][6][32]  adjoint of a body's summed force, torque
   float* gpub;   // [B][18][32] a child's adjoints of its parent's x1, R, v, w
   float* gacc;   // [B][6][32]  adjoint of a body's contact velocity update (pairs)
-  float* gpair;  // [B][18][32] pair adjoints of a body's x1, R, v, w (atomics)
+  float* pairg;  // workspace [P][2][18][32]: a pair's adjoints of body a's and body b's x1, R, v, w
 };
 
 __device__ __forceinline__ void load_body_ws(const float* p, int stride, Body& s) {
@@ -287,18 +295,18 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
         GSide& G = side == 0 ? GA : GB;
         const Pub X = read_pub(gm, body, lane);
         inv_inertia_bwd(X.R, bodies[body].inv_I, G.I, G.R);
-        float* o = bm.gpair + (body * 18) * 32 + lane;
-        atomicAdd(o + 0 * 32, G.x.x);
-        atomicAdd(o + 1 * 32, G.x.y);
-        atomicAdd(o + 2 * 32, G.x.z);
+        float* o = bm.pairg + ((int64_t)(k * 2 + side) * 18) * 32 + lane;
+        o[0 * 32] = G.x.x;
+        o[1 * 32] = G.x.y;
+        o[2 * 32] = G.x.z;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) atomicAdd(o + (3 + i) * 32, G.R.m[i]);
-        atomicAdd(o + 12 * 32, G.v.x);
-        atomicAdd(o + 13 * 32, G.v.y);
-        atomicAdd(o + 14 * 32, G.v.z);
-        atomicAdd(o + 15 * 32, G.w.x);
-        atomicAdd(o + 16 * 32, G.w.y);
-        atomicAdd(o + 17 * 32, G.w.z);
+        for (int i = 0; i < 9; ++i) o[(3 + i) * 32] = G.R.m[i];
+        o[12 * 32] = G.v.x;
+        o[13 * 32] = G.v.y;
+        o[14 * 32] = G.v.z;
+        o[15 * 32] = G.w.x;
+        o[16 * 32] = G.w.y;
+        o[17 * 32] = G.w.z;
       }
     }
   }
@@ -312,15 +320,15 @@ __device__ __forceinline__ void bwd_substep(const SysP& S, const BodyP* bodies, 
     gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
     gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
   }
-  if (kGeneral && (bp.flags & kInPair)) {
-    float* o = bm.gpair + (b * 18) * 32 + lane;
+  for (int i = 0; kGeneral && i < bp.n_bpairs; ++i) {  // the own pairs' adjoints, in the body's pair order
+    const int code = bp.bpair[i];
+    if (gm.slot4(code >> 1, 1)[lane].z == 0.f) continue;  // no contact: the pair wrote nothing for this lane
+    const float* o = bm.pairg + ((int64_t)code * 18) * 32 + lane;
     gx1 = gx1 + mk3(o[0], o[32], o[64]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) gR.m[i] += o[(3 + i) * 32];
+    for (int j = 0; j < 9; ++j) gR.m[j] += o[(3 + j) * 32];
     gvm = gvm + mk3(o[12 * 32], o[13 * 32], o[14 * 32]);
     gwm = gwm + mk3(o[15 * 32], o[16 * 32], o[17 * 32]);
-#pragma unroll
-    for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
   inv_inertia_bwd(f.R, bp.inv_I, gI, gR);
   if (kGeneral && S.gyro) inv_inertia_bwd(f.R, bp.I, gIw, gR);
@@ -507,7 +515,7 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
   bm.gwr = gbase + bwd_fwd_floats(B, P, false);
   bm.gpub = bm.gwr + B * 6 * 32;
   bm.gacc = bm.gpub + B * 18 * 32;
-  bm.gpair = bm.gacc + B * 6 * 32;
+  bm.pairg = ws + ws_pairg_off(B, P, K, nsub);
   const int bar = 1 + g, nthr = 32 * B;
   const BodyP& bp = bodies[b];
   const int stride = B * 32;
@@ -520,11 +528,6 @@ __device__ __forceinline__ void rollout_bwd_body(const Launch& L) {
     if (bp.flags & kHasParent) hr = hinge_regs(bp);
     if (bp.n_points > 0) pr[0] = point_regs(bp.pt[0]);
     if (bp.n_points > 1) pr[1] = point_regs(bp.pt[1]);
-  }
-  if (kGeneral && P > 0) {
-    float* o = bm.gpair + (b * 18) * 32 + lane;
-#pragma unroll
-    for (int i = 0; i < 18; ++i) o[i * 32] = 0.f;
   }
   const int nseg = (T + K - 1) / K;
   const int seg_hi = chunked ? nseg - c * L.sc.chunk_steps : nseg;

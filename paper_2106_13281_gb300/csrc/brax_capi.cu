@@ -941,9 +941,9 @@ int rollout_impl(const brax_system* s, int64_t n_envs, int32_t T, int32_t K, con
   L.T = T;
   L.K = K < 1 ? 1 : K;
   // Two environments per thread whenever the system has that kernel and it
-  // is switched on, checkpointing rollouts included: the reverse pass then
-  // rebuilds a checkpoint segment's step states with this same kernel
-  // (rollout_backward_impl), so gradients do not depend on K.
+  // is switched on, checkpointing rollouts included: the reverse pass
+  // rebuilds a checkpoint segment's step states with the kernel that wrote
+  // the checkpoints (rollout_backward_impl), so gradients do not depend on K.
   if (s->pair_mode == 1) {
     Seg sg = make_seg(s, s->pair_groups, n_envs);
     const int64_t per_cta = 64LL * s->pair_groups;
@@ -1293,9 +1293,17 @@ size_t bwd_kernel_ws_bytes(const brax_system* s, int64_t n_envs, int32_t K) {
 }
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Whether the reverse pass rebuilds each checkpoint segment's step states
-// with the two-environments kernel (the one that wrote the checkpoints)
-// instead of recomputing them inside the reverse kernel.
-bool bwd_by_segments(const brax_system* s, int32_t K) { return s->pair_mode == 1 && K > 1; }
+// with the forward kernel (the one that wrote the checkpoints) instead of
+// recomputing them inside the reverse kernel: whenever a segment has more
+// than one step.  The reverse kernel's own step arithmetic agrees with the
+// forward kernels' to FP32 rounding but not always bit for bit (the compiled
+// code of each kernel decides where a multiply and an add fuse; the biped's
+// differs), so only the forward kernel reproduces the forward's step states
+// exactly.
+bool bwd_by_segments(const brax_system* s, int32_t K) {
+  (void)s;
+  return K > 1;
+}
 // Scratch of brax_rollout_backward for (n_envs, K), K already at most T.
 // Rebuilding segments: the reverse kernel's scratch for K = 1, the step
 // states of one segment [K][N][B][13] and two state adjoints [N][B][13]
@@ -1346,7 +1354,7 @@ int rollout_backward_impl(const brax_system* s, int64_t n_envs, int32_t T, int32
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
     return fail(BRAX_ERR_WORKSPACE, "brax_rollout_backward: workspace must be 256-byte aligned");
   if (bwd_by_segments(s, Ke)) {
-    // Checkpoint segments, last first: the two-environments kernel (which
+    // Checkpoint segments, last first: the forward kernel (the one that
     // wrote the checkpoints) rebuilds the segment's step states from its
     // checkpoint, K - 1 steps with a checkpoint every step plus the state
     // after them; then the reverse kernel runs the segment with K = 1 and
