@@ -468,8 +468,8 @@ __device__ __forceinline__ void joint3_bwd(const BodyP& bp, const Pub& pp, const
 }
 
 // ------------------------------------------------------------------ body-body pairs
-// Adjoint state of one side of a pair (to be added to that body's
-// accumulators through shared-memory atomics).
+// Adjoint state of one side of a pair (written to the workspace; the body
+// adds its pairs' contributions in its own pair order).
 struct GSide {
   V3 x, v, w;
   M3 R;
